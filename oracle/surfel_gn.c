@@ -1,0 +1,535 @@
+/*
+ * FP64 CPU ORACLE of the per-surfel Gauss-Newton photometric optimisation of
+ * "Dense monocular SLAM by direct surfel optimization" (Sec. 2.1-2.4).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this code.  It shares nothing with the
+ * CUDA library: no headers, helpers, tables or pre/post-processing.  It is
+ * written for a reader who checks it against the paper by eye: one function
+ * per step, each step in the paper's order and notation, everything in double
+ * precision, no blocking, fusion or reordering.
+ *
+ * Conventions where the paper is silent or garbled (each is a reading of the
+ * paper, not something it states):
+ *  - pixel centres at integer coordinates; K = [fx 0 cx; 0 fy cy; 0 0 1];
+ *  - surfel s is the P x P tile (tx, ty), s = ty * (W / P) + tx, with centre
+ *    u_s = (tx P + (P-1)/2, ty P + (P-1)/2) and ray r_s = K^-1 (u_s, 1)
+ *    (z = 1, as in the frame-change section where r_s = pi(p));
+ *  - the reprojection of Eq. 6 is read with pi and pi^-1 in their defined roles:
+ *    u_p = pi(K (R p_u + t)) with p_u = r_u / id_u;
+ *  - the projection derivative printed after Eq. 8 is replaced by the true
+ *    derivative of pi at q, and the derivative of q with respect to id_u keeps
+ *    its factor -1/id_u^2;
+ *  - Eq. 9's first line is read with r_u and p_s in their correct places:
+ *    d id_u / d n = r_u / (p_s . n) - (r_u . n) p_s / (p_s . n)^2;
+ *  - gradients are central differences; a sample is valid when h_z > 0 and all
+ *    four bilinear taps lie in [1, W-2] x [1, H-2], i.e. 1 <= x < W-2 and
+ *    1 <= y < H-2; invalid samples are dropped;
+ *  - Huber threshold k and Levenberg-Marquardt lambda are parameters; the
+ *    damping is H + lambda diag(m, m, H33) with m = (H11 + H22) / 2, which does
+ *    not depend on the choice of tangent basis;
+ *  - the normal step (Sec. 2.4, last paragraph) is taken in the tangent plane of
+ *    n with the orthonormal basis of Duff et al., "Building an Orthonormal
+ *    Basis, Revisited" (JCGT 2017), then n is renormalised;
+ *  - Eq. 3 is unchanged when n changes sign, so after each update the normal is
+ *    turned to face the camera (n . r_s < 0); this fixes the representation only;
+ *  - seeding (Sec. 2.3): one Jacobi pass over tiles marked TO_SEED, using the
+ *    8-connected tiles that were VALID before the pass as the neighbours.
+ *
+ * Parity pins: every function below is pinned by a test in tests/ against
+ * closed forms, finite differences, library routines or brute force; the
+ * constants k, lambda and min_residuals are conventions ("parity unpinned" for
+ * their values, not for the arithmetic).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { ST_EMPTY = 0, ST_VALID = 1, ST_TO_SEED = 2 };
+enum {
+    OUT_OK = 0, OUT_EMPTY = 1, OUT_UNSEEDED = 2, OUT_UNDERDETERMINED = 3,
+    OUT_SINGULAR = 4, OUT_STEP_REJECTED = 5, OUT_SEEDED_FLAG = 0x40
+};
+
+typedef struct {
+    double huber_k;
+    double lm_lambda;
+    int optimize_normal;
+    int min_residuals;
+} orc_params;
+
+typedef struct {
+    int W, H, P, F;
+    double fx, fy, cx, cy;
+    double* kf;   /* keyframe intensity, H*W */
+    double* I;    /* frame intensity, F*H*W */
+    double* gx;   /* frame gradient along x, F*H*W */
+    double* gy;   /* frame gradient along y, F*H*W */
+    double* T;    /* F poses, row-major [R|t], keyframe -> frame */
+} orc_problem;
+
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* ---------------------------------------------------------------- image terms */
+
+/* Image gradient by central differences; border rows and columns get 0. */
+void orc_gradients(int W, int H, const double* img, double* gx, double* gy) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            long i = (long)y * W + x;
+            gx[i] = (x >= 1 && x <= W - 2) ? 0.5 * (img[i + 1] - img[i - 1]) : 0.0;
+            gy[i] = (y >= 1 && y <= H - 2) ? 0.5 * (img[i + W] - img[i - W]) : 0.0;
+        }
+}
+
+/* Bilinear interpolation at (x, y); the caller guarantees all four taps are inside. */
+double orc_bilinear(int W, const double* img, double x, double y) {
+    double x0 = floor(x), y0 = floor(y);
+    double ax = x - x0, ay = y - y0;
+    long i = (long)y0 * W + (long)x0;
+    double v00 = img[i], v10 = img[i + 1], v01 = img[i + W], v11 = img[i + W + 1];
+    return (1.0 - ay) * ((1.0 - ax) * v00 + ax * v10) + ay * ((1.0 - ax) * v01 + ax * v11);
+}
+
+/* Huber norm (Eq. 5) and its IRLS weight w = rho'(r) / r. */
+void orc_huber(double r, double k, double* rho, double* w) {
+    double a = fabs(r);
+    if (a <= k) {
+        *rho = 0.5 * r * r;
+        *w = 1.0;
+    } else {
+        *rho = k * (a - 0.5 * k);
+        *w = k / a;
+    }
+}
+
+/* ---------------------------------------------------------------- geometry */
+
+/* Eq. 2: ray of pixel u, r_u = K^-1 (u_x, u_y, 1). */
+void orc_ray(double fx, double fy, double cx, double cy, double ux, double uy, double r[3]) {
+    r[0] = (ux - cx) / fx;
+    r[1] = (uy - cy) / fy;
+    r[2] = 1.0;
+}
+
+/* Eq. 3: inverse depth of ray r_u on the plane of surfel (r_s, id_s, n). */
+double orc_inv_depth(const double r_u[3], const double r_s[3], double id_s, const double n[3]) {
+    double p_s[3] = {r_s[0] / id_s, r_s[1] / id_s, r_s[2] / id_s}; /* Eq. 1 */
+    return dot3(r_u, n) / dot3(p_s, n);
+}
+
+/* Eq. 9 (first line corrected): d id_u / d n and d id_u / d id_s. */
+void orc_inv_depth_derivative(const double r_u[3], const double r_s[3], double id_s, const double n[3],
+                              double d_dn[3], double* d_did) {
+    double p_s[3] = {r_s[0] / id_s, r_s[1] / id_s, r_s[2] / id_s};
+    double psn = dot3(p_s, n), run = dot3(r_u, n);
+    for (int i = 0; i < 3; ++i) d_dn[i] = r_u[i] / psn - run * p_s[i] / (psn * psn);
+    *d_did = run / dot3(r_s, n);
+}
+
+/*
+ * Eq. 6: u_p = pi(K (R p_u + t)), p_u = r_u / id_u, with its derivative
+ * d u_p / d id_u by the chain rule through q = R p_u + t (Eq. 8 terms).
+ * Returns q_z (the point's depth in the frame); u_p and its derivative are
+ * only meaningful when q_z > 0.
+ */
+double orc_warp(double fx, double fy, double cx, double cy, const double T[12], const double r_u[3], double id_u,
+                double u_p[2], double du_did[2]) {
+    double p_u[3] = {r_u[0] / id_u, r_u[1] / id_u, r_u[2] / id_u};
+    double q[3], dq[3];
+    for (int i = 0; i < 3; ++i) {
+        q[i] = T[4 * i + 0] * p_u[0] + T[4 * i + 1] * p_u[1] + T[4 * i + 2] * p_u[2] + T[4 * i + 3];
+        /* d q / d id_u = -R r_u / id_u^2 */
+        dq[i] = -(T[4 * i + 0] * r_u[0] + T[4 * i + 1] * r_u[1] + T[4 * i + 2] * r_u[2]) / (id_u * id_u);
+    }
+    /* pi(K q) = (fx q_x / q_z + cx, fy q_y / q_z + cy) */
+    u_p[0] = fx * q[0] / q[2] + cx;
+    u_p[1] = fy * q[1] / q[2] + cy;
+    /* d pi(K q) / d q = [fx/q_z, 0, -fx q_x/q_z^2; 0, fy/q_z, -fy q_y/q_z^2] */
+    du_did[0] = fx * (dq[0] / q[2] - q[0] * dq[2] / (q[2] * q[2]));
+    du_did[1] = fy * (dq[1] / q[2] - q[1] * dq[2] / (q[2] * q[2]));
+    return q[2];
+}
+
+/* Orthonormal tangent basis (t1, t2) of a unit normal n (Duff et al. 2017). */
+void orc_tangent_basis(const double n[3], double t1[3], double t2[3]) {
+    double sign = copysign(1.0, n[2]);
+    double a = -1.0 / (sign + n[2]);
+    double b = n[0] * n[1] * a;
+    t1[0] = 1.0 + sign * n[0] * n[0] * a;
+    t1[1] = sign * b;
+    t1[2] = -sign * n[0];
+    t2[0] = b;
+    t2[1] = sign + n[1] * n[1] * a;
+    t2[2] = -n[1];
+}
+
+/* Solve A x = b for symmetric positive definite 3x3 A (packed a00 a01 a02 a11 a12 a22)
+ * by Cholesky factorisation.  Returns 0 if a pivot is not positive. */
+int orc_cholesky_solve3(const double A[6], const double b[3], double x[3]) {
+    double a00 = A[0], a01 = A[1], a02 = A[2], a11 = A[3], a12 = A[4], a22 = A[5];
+    if (!(a00 > 0.0)) return 0;
+    double l00 = sqrt(a00);
+    double l10 = a01 / l00, l20 = a02 / l00;
+    double d1 = a11 - l10 * l10;
+    if (!(d1 > 0.0)) return 0;
+    double l11 = sqrt(d1);
+    double l21 = (a12 - l20 * l10) / l11;
+    double d2 = a22 - l20 * l20 - l21 * l21;
+    if (!(d2 > 0.0)) return 0;
+    double l22 = sqrt(d2);
+    double y0 = b[0] / l00;
+    double y1 = (b[1] - l10 * y0) / l11;
+    double y2 = (b[2] - l20 * y0 - l21 * y1) / l22;
+    x[2] = y2 / l22;
+    x[1] = (y1 - l21 * x[2]) / l11;
+    x[0] = (y0 - l10 * x[1] - l20 * x[2]) / l00;
+    return 1;
+}
+
+/* ---------------------------------------------------------------- problem */
+
+void* orc_problem_create(int W, int H, int P, double fx, double fy, double cx, double cy, const float* keyframe,
+                         int F, const float* frames, const double* poses) {
+    orc_problem* pb = (orc_problem*)calloc(1, sizeof(orc_problem));
+    long n = (long)W * H;
+    pb->W = W; pb->H = H; pb->P = P; pb->F = F;
+    pb->fx = fx; pb->fy = fy; pb->cx = cx; pb->cy = cy;
+    pb->kf = (double*)malloc(sizeof(double) * n);
+    pb->I = (double*)malloc(sizeof(double) * n * (F > 0 ? F : 1));
+    pb->gx = (double*)malloc(sizeof(double) * n * (F > 0 ? F : 1));
+    pb->gy = (double*)malloc(sizeof(double) * n * (F > 0 ? F : 1));
+    pb->T = (double*)malloc(sizeof(double) * 12 * (F > 0 ? F : 1));
+    for (long i = 0; i < n; ++i) pb->kf[i] = keyframe[i];
+    for (int f = 0; f < F; ++f) {
+        for (long i = 0; i < n; ++i) pb->I[f * n + i] = frames[f * n + i];
+        orc_gradients(W, H, pb->I + f * n, pb->gx + f * n, pb->gy + f * n);
+        memcpy(pb->T + 12 * f, poses + 12 * f, 12 * sizeof(double));
+    }
+    return pb;
+}
+
+void orc_problem_destroy(void* p) {
+    orc_problem* pb = (orc_problem*)p;
+    if (!pb) return;
+    free(pb->kf); free(pb->I); free(pb->gx); free(pb->gy); free(pb->T);
+    free(pb);
+}
+
+static void tile_centre_ray(const orc_problem* pb, int s, double r_s[3]) {
+    int TX = pb->W / pb->P;
+    int tx = s % TX, ty = s / TX;
+    double ux = tx * pb->P + 0.5 * (pb->P - 1), uy = ty * pb->P + 0.5 * (pb->P - 1);
+    orc_ray(pb->fx, pb->fy, pb->cx, pb->cy, ux, uy, r_s);
+}
+
+/*
+ * One Gauss-Newton evaluation of surfel s at parameters (id_s, n): the Huber cost
+ * of Eq. 5 over the tile's pixels and all frames, and the normal equations
+ * H = sum w J J^T, g = sum w J r with J = (grad I . d u_p / d id_u) * (d id_u / d theta),
+ * theta = (step along t1, step along t2, id_s) (Eqs. 7-9).
+ * Also returns the same sums for the unconstrained 4-vector J4 = (grad I . d u_p/d id_u) *
+ * (d id_u / d n, d id_u / d id_s) (packed upper triangle of 4x4, 10 entries), and the
+ * smallest distance of any valid sample to the validity bounds (pixels).
+ */
+void orc_eval_surfel(const void* p, const orc_params* prm, int s, double id_s, const double n[3], double H[6],
+                     double g[3], double* E, int* cnt, double* margin, double H4[10], double g4[4]) {
+    const orc_problem* pb = (const orc_problem*)p;
+    int W = pb->W, Hh = pb->H, P = pb->P, TX = W / P;
+    long npx = (long)W * Hh;
+    int tx = s % TX, ty = s / TX;
+    double r_s[3], t1[3], t2[3];
+    tile_centre_ray(pb, s, r_s);
+    orc_tangent_basis(n, t1, t2);
+    for (int i = 0; i < 6; ++i) H[i] = 0.0;
+    for (int i = 0; i < 3; ++i) g[i] = 0.0;
+    if (H4) for (int i = 0; i < 10; ++i) H4[i] = 0.0;
+    if (g4) for (int i = 0; i < 4; ++i) g4[i] = 0.0;
+    *E = 0.0;
+    *cnt = 0;
+    double mg = INFINITY;
+    for (int py = 0; py < P; ++py)
+        for (int px = 0; px < P; ++px) {
+            int ux = tx * P + px, uy = ty * P + py;
+            double r_u[3];
+            orc_ray(pb->fx, pb->fy, pb->cx, pb->cy, ux, uy, r_u);
+            double id_u = orc_inv_depth(r_u, r_s, id_s, n);
+            if (!(id_u > 0.0) || !isfinite(id_u)) continue;
+            double d_dn[3], d_did;
+            orc_inv_depth_derivative(r_u, r_s, id_s, n, d_dn, &d_did);
+            if (!prm->optimize_normal) d_dn[0] = d_dn[1] = d_dn[2] = 0.0; /* depth-only ablation */
+            double Jt[3] = {dot3(d_dn, t1), dot3(d_dn, t2), d_did};
+            double J4t[4] = {d_dn[0], d_dn[1], d_dn[2], d_did};
+            double Ikf = pb->kf[(long)uy * W + ux];
+            for (int f = 0; f < pb->F; ++f) {
+                double u_p[2], du[2];
+                double qz = orc_warp(pb->fx, pb->fy, pb->cx, pb->cy, pb->T + 12 * f, r_u, id_u, u_p, du);
+                if (!(qz > 0.0)) continue;
+                if (!(u_p[0] >= 1.0 && u_p[0] < W - 2.0 && u_p[1] >= 1.0 && u_p[1] < Hh - 2.0)) continue;
+                double m = fmin(fmin(u_p[0] - 1.0, (W - 2.0) - u_p[0]), fmin(u_p[1] - 1.0, (Hh - 2.0) - u_p[1]));
+                if (m < mg) mg = m;
+                const double* If = pb->I + f * npx;
+                double Iv = orc_bilinear(W, If, u_p[0], u_p[1]);
+                double gxv = orc_bilinear(W, pb->gx + f * npx, u_p[0], u_p[1]);
+                double gyv = orc_bilinear(W, pb->gy + f * npx, u_p[0], u_p[1]);
+                double r = Iv - Ikf;
+                double rho, w;
+                orc_huber(r, prm->huber_k, &rho, &w);
+                double dI_did = gxv * du[0] + gyv * du[1]; /* Eq. 8 */
+                double J[3] = {dI_did * Jt[0], dI_did * Jt[1], dI_did * Jt[2]}; /* Eq. 7 */
+                int k = 0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = a; b < 3; ++b) H[k++] += w * J[a] * J[b];
+                for (int a = 0; a < 3; ++a) g[a] += w * J[a] * r;
+                if (H4 && g4) {
+                    double J4[4];
+                    for (int a = 0; a < 4; ++a) J4[a] = dI_did * J4t[a];
+                    k = 0;
+                    for (int a = 0; a < 4; ++a)
+                        for (int b = a; b < 4; ++b) H4[k++] += w * J4[a] * J4[b];
+                    for (int a = 0; a < 4; ++a) g4[a] += w * J4[a] * r;
+                }
+                *E += rho;
+                *cnt += 1;
+            }
+        }
+    if (margin) *margin = mg;
+}
+
+/*
+ * Levenberg-Marquardt damped Gauss-Newton step (Sec. 2.4): solve
+ * (H + lambda diag(m, m, H33)) delta = -g, m = (H11 + H22) / 2.  In the depth-only
+ * ablation the normal block is empty and the step is the scalar -g3 / ((1 + lambda) H33).
+ * Returns 0 when the damped matrix is not positive definite.
+ */
+int orc_damped_step(const double H[6], const double g[3], double lambda, int optimize_normal, double delta[3]) {
+    if (!optimize_normal) {
+        double h = (1.0 + lambda) * H[5];
+        delta[0] = delta[1] = 0.0;
+        if (!(h > 0.0)) return 0;
+        delta[2] = -g[2] / h;
+        return 1;
+    }
+    double m = 0.5 * (H[0] + H[3]);
+    double A[6] = {H[0] + lambda * m, H[1], H[2], H[3] + lambda * m, H[4], H[5] + lambda * H[5]};
+    double rhs[3] = {-g[0], -g[1], -g[2]};
+    return orc_cholesky_solve3(A, rhs, delta);
+}
+
+/* Sec. 2.4, last paragraph: n <- normalize(n + d1 t1 + d2 t2), id_s <- id_s + d3. */
+void orc_apply_step(const double n[3], double id_s, const double delta[3], double n_out[3], double* id_out) {
+    double t1[3], t2[3];
+    orc_tangent_basis(n, t1, t2);
+    double v[3];
+    for (int i = 0; i < 3; ++i) v[i] = n[i] + delta[0] * t1[i] + delta[1] * t2[i];
+    double len = sqrt(dot3(v, v));
+    for (int i = 0; i < 3; ++i) n_out[i] = v[i] / len;
+    *id_out = id_s + delta[2];
+}
+
+/*
+ * Gauss-Newton on every surfel whose status is not EMPTY/UNSEEDED.
+ * id (S), n (3S) are updated in place.  status (S) is read (EMPTY/UNSEEDED and the
+ * SEEDED flag are kept) and receives the outcome of the last iteration: OK,
+ * UNDERDETERMINED (fewer than min_residuals valid samples), SINGULAR (damped matrix
+ * not positive definite) or STEP_REJECTED (non-positive or non-finite new id_s / n).
+ * After the iterations, one more evaluation at the returned parameters gives cost (the
+ * "last residual" kept with each surfel, Sec. 2.1) and nres.  Optional per-surfel
+ * diagnostics: margin (smallest distance of any sample used to the validity bounds,
+ * over all evaluations) and H_last (6 per surfel, undamped H of the last iteration).
+ * Returns the number of threads used.
+ */
+int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthreads, double* id, double* n,
+                     uint8_t* status, double* cost, int32_t* nres, double* margin, double* H_last) {
+    const orc_problem* pb = (const orc_problem*)p;
+    int S = (pb->W / pb->P) * (pb->H / pb->P);
+    int used = 1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+    {
+#pragma omp single
+        used = omp_get_num_threads();
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int s = 0; s < S; ++s) {
+            int st = status[s] & 0x3f;
+            int flags = status[s] & OUT_SEEDED_FLAG;
+            double mg = INFINITY;
+            if (st == OUT_EMPTY || st == OUT_UNSEEDED) {
+                cost[s] = 0.0;
+                nres[s] = 0;
+                if (margin) margin[s] = mg;
+                continue;
+            }
+            double ids = id[s], ns[3] = {n[3 * s], n[3 * s + 1], n[3 * s + 2]};
+            int outcome = OUT_OK;
+            double H[6], g[3], E, m;
+            int cnt;
+            if (H_last) for (int i = 0; i < 6; ++i) H_last[6 * s + i] = 0.0;
+            for (int it = 0; it < iters; ++it) {
+                orc_eval_surfel(pb, prm, s, ids, ns, H, g, &E, &cnt, &m, NULL, NULL);
+                if (m < mg) mg = m;
+                if (H_last) for (int i = 0; i < 6; ++i) H_last[6 * s + i] = H[i];
+                if (cnt < prm->min_residuals) {
+                    outcome = OUT_UNDERDETERMINED;
+                    continue;
+                }
+                double delta[3];
+                if (!orc_damped_step(H, g, prm->lm_lambda, prm->optimize_normal, delta)) {
+                    outcome = OUT_SINGULAR;
+                    continue;
+                }
+                double n_new[3], id_new;
+                if (prm->optimize_normal) {
+                    orc_apply_step(ns, ids, delta, n_new, &id_new);
+                } else { /* depth-only ablation: the normal is not a parameter */
+                    n_new[0] = ns[0]; n_new[1] = ns[1]; n_new[2] = ns[2];
+                    id_new = ids + delta[2];
+                }
+                if (!(id_new > 0.0) || !isfinite(id_new) || !isfinite(n_new[0]) || !isfinite(n_new[1]) ||
+                    !isfinite(n_new[2])) {
+                    outcome = OUT_STEP_REJECTED;
+                    continue;
+                }
+                /* Eq. 3 does not change when n changes sign: keep the representative that
+                 * faces the camera, n . r_s < 0. */
+                double r_s[3];
+                tile_centre_ray(pb, s, r_s);
+                if (dot3(n_new, r_s) > 0.0) {
+                    n_new[0] = -n_new[0]; n_new[1] = -n_new[1]; n_new[2] = -n_new[2];
+                }
+                ids = id_new;
+                ns[0] = n_new[0]; ns[1] = n_new[1]; ns[2] = n_new[2];
+                outcome = OUT_OK;
+            }
+            orc_eval_surfel(pb, prm, s, ids, ns, H, g, &E, &cnt, &m, NULL, NULL);
+            if (m < mg) mg = m;
+            id[s] = ids;
+            n[3 * s] = ns[0]; n[3 * s + 1] = ns[1]; n[3 * s + 2] = ns[2];
+            status[s] = (uint8_t)(outcome | flags);
+            cost[s] = E;
+            nres[s] = cnt;
+            if (margin) margin[s] = mg;
+        }
+#ifdef _OPENMP
+    }
+#endif
+    return used;
+}
+
+/*
+ * Sec. 2.3: neighbour seeding, one Jacobi pass.  For each TO_SEED tile, the 8-connected
+ * tiles that are VALID in state_in are its neighbours.  The new inverse depth is the
+ * mean, over neighbours, of Eq. 3 evaluated at the new tile's centre ray against the
+ * neighbour's plane (values that are not finite and positive are skipped).  The new
+ * normal is the normalised sum of the neighbours' normals, each first turned to face
+ * the camera (n . r_s < 0).  Outputs: status_out = OK | SEEDED flag for seeded tiles,
+ * UNSEEDED when no neighbour gives a value or the normal sum is shorter than 1e-6,
+ * EMPTY for empty tiles and OK for VALID tiles (whose id/n are copied).
+ */
+void orc_seed(const void* p, const double* id_in, const double* n_in, const uint8_t* state_in, double* id_out,
+              double* n_out, uint8_t* status_out) {
+    const orc_problem* pb = (const orc_problem*)p;
+    int TX = pb->W / pb->P, TY = pb->H / pb->P, S = TX * TY;
+    for (int s = 0; s < S; ++s) {
+        id_out[s] = id_in[s];
+        for (int i = 0; i < 3; ++i) n_out[3 * s + i] = n_in[3 * s + i];
+        if (state_in[s] == ST_VALID) {
+            status_out[s] = OUT_OK;
+            continue;
+        }
+        if (state_in[s] != ST_TO_SEED) {
+            status_out[s] = OUT_EMPTY;
+            continue;
+        }
+        int tx = s % TX, ty = s / TX;
+        double r_new[3];
+        tile_centre_ray(pb, s, r_new);
+        double id_sum = 0.0, nsum[3] = {0, 0, 0};
+        int nid = 0, nn = 0;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0) continue;
+                int qx = tx + dx, qy = ty + dy;
+                if (qx < 0 || qy < 0 || qx >= TX || qy >= TY) continue;
+                int q = qy * TX + qx;
+                if (state_in[q] != ST_VALID) continue;
+                double r_q[3];
+                tile_centre_ray(pb, q, r_q);
+                const double* nq = n_in + 3 * q;
+                double v = orc_inv_depth(r_new, r_q, id_in[q], nq);
+                if (isfinite(v) && v > 0.0) {
+                    id_sum += v;
+                    nid++;
+                }
+                double sgn = dot3(nq, r_q) < 0.0 ? 1.0 : -1.0;
+                for (int i = 0; i < 3; ++i) nsum[i] += sgn * nq[i];
+                nn++;
+            }
+        double len = sqrt(dot3(nsum, nsum));
+        if (nid == 0 || nn == 0 || !(len >= 1e-6)) {
+            status_out[s] = OUT_UNSEEDED;
+            id_out[s] = 0.0;
+            n_out[3 * s] = n_out[3 * s + 1] = n_out[3 * s + 2] = 0.0;
+            continue;
+        }
+        id_out[s] = id_sum / nid;
+        for (int i = 0; i < 3; ++i) n_out[3 * s + i] = nsum[i] / len;
+        status_out[s] = OUT_OK | OUT_SEEDED_FLAG;
+    }
+}
+
+/*
+ * Sec. 2.2: per-pixel inverse depth of the keyframe from the surfels (Eq. 3), with
+ * the index of the generating surfel.  Tiles do not overlap, so every pixel of a
+ * full tile belongs to its tile's surfel.  Pixels outside full tiles, of surfels
+ * whose status is EMPTY/UNSEEDED, or with a non-finite / non-positive value get 0 and -1.
+ */
+void orc_depth_map(const void* p, const double* id, const double* n, const uint8_t* status, double* inv_depth,
+                   int32_t* sidx) {
+    const orc_problem* pb = (const orc_problem*)p;
+    int W = pb->W, Hh = pb->H, P = pb->P, TX = W / P, TY = Hh / P;
+    for (long i = 0; i < (long)W * Hh; ++i) {
+        inv_depth[i] = 0.0;
+        sidx[i] = -1;
+    }
+    for (int s = 0; s < TX * TY; ++s) {
+        int st = status[s] & 0x3f;
+        if (st == OUT_EMPTY || st == OUT_UNSEEDED) continue;
+        int tx = s % TX, ty = s / TX;
+        double r_s[3];
+        tile_centre_ray(pb, s, r_s);
+        for (int py = 0; py < P; ++py)
+            for (int px = 0; px < P; ++px) {
+                int ux = tx * P + px, uy = ty * P + py;
+                double r_u[3];
+                orc_ray(pb->fx, pb->fy, pb->cx, pb->cy, ux, uy, r_u);
+                double v = orc_inv_depth(r_u, r_s, id[s], n + 3 * s);
+                if (!isfinite(v) || !(v > 0.0)) continue;
+                inv_depth[(long)uy * W + ux] = v;
+                sidx[(long)uy * W + ux] = s;
+            }
+    }
+}
+
+/*
+ * Huber cost of Eq. 5 for surfel s at m candidate parameter sets (ids[i], normals[3i..3i+2]).
+ * Used by the brute-force scan that pins the Gauss-Newton minimiser; each candidate is a
+ * plain call of orc_eval_surfel.  Writes E[i] and the valid sample count cnt[i].
+ */
+void orc_cost_grid(const void* p, const orc_params* prm, int s, long m, const double* ids, const double* normals,
+                   double* E, int32_t* cnt) {
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < m; ++i) {
+        double H[6], g[3], e, mg;
+        int c;
+        orc_eval_surfel(p, prm, s, ids[i], normals + 3 * i, H, g, &e, &c, &mg, NULL, NULL);
+        E[i] = e;
+        cnt[i] = c;
+    }
+}
