@@ -1,0 +1,207 @@
+/*
+ * sgn.h -- C ABI of libsgn, a CUDA (sm_103a) implementation of per-surfel Gauss-Newton
+ * photometric optimisation for dense monocular depth and normal estimation
+ * ("Dense monocular SLAM by direct surfel optimization", Sec. 2).
+ *
+ * Model.  A keyframe of W x H pixels is cut into P x P tiles; tile s = ty * (W / P) + tx
+ * (row-major, full tiles only) is surfel s.  A surfel is a plane given by its inverse depth
+ * id_s along the ray r_s = K^-1 (u_s, 1) of the tile centre u_s = (tx P + (P-1)/2,
+ * ty P + (P-1)/2) and its unit normal n_s, both in keyframe camera coordinates (Sec. 2.1,
+ * Eq. 1).  Pixel centres sit at integer coordinates.  Observing frames n = 0..F-1 come with
+ * the pose T = [R | t] (row-major 3 x 4, doubles) that maps keyframe points into frame
+ * coordinates.  The library minimises, per surfel, the Huber-normed photometric error of
+ * Eq. 5 over the tile's pixels warped into every frame through the plane (Eq. 6), by
+ * Levenberg-Marquardt damped Gauss-Newton steps on (two tangent directions of n_s, id_s)
+ * (Eqs. 7-9, Sec. 2.4), seeds new surfels from their neighbours (Sec. 2.3) and renders the
+ * per-pixel inverse depth of Eq. 3 (Sec. 2.2).
+ *
+ * Memory.  The caller owns all memory.  A plan describes one keyframe problem; the caller
+ * asks sgn_plan_workspace_bytes() for the device workspace size, allocates it (any
+ * allocator) and binds it with a CUDA stream.  libsgn allocates no device memory.  Host
+ * pointers passed in stay owned by the caller; copies from/to host memory are enqueued on
+ * the bound stream (page-locked host memory makes them asynchronous), so host buffers must
+ * stay valid until sgn_sync() returns.  Device pointers passed in must stay valid until
+ * the work that reads them has run (sgn_sync() or a stream synchronisation).
+ *
+ * Errors.  Every call returns an sgn_status.  Arguments are validated on the host before
+ * anything is enqueued; a rejected call changes nothing.  Asynchronous CUDA errors surface
+ * as SGN_ERR_CUDA at the next call that checks the stream (sgn_sync, reads).  A
+ * human-readable message for the last failure of the calling thread is available from
+ * sgn_last_error().  Per-surfel numerical outcomes are status codes, not errors.
+ *
+ * Threads.  A plan (and a batch) must be used by one host thread at a time.
+ */
+#ifndef SGN_H
+#define SGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SGN_MAX_FRAMES 16
+#define SGN_ABI_VERSION 1
+
+typedef enum {
+    SGN_OK = 0,
+    SGN_ERR_INVALID_ARGUMENT = -1,   /* a size, pointer, pitch, pose or option is not acceptable */
+    SGN_ERR_NOT_BOUND = -2,          /* the plan has no workspace/stream yet */
+    SGN_ERR_WORKSPACE_TOO_SMALL = -3,
+    SGN_ERR_CUDA = -4,               /* a CUDA runtime call or kernel failed */
+    SGN_ERR_TIMEOUT = -5,            /* sgn_sync deadline passed, or a device-side wait gave up */
+    SGN_ERR_ADMISSION = -6,          /* a request does not fit the memory budget */
+    SGN_ERR_STATE = -7               /* call out of order (e.g. run before intrinsics/frames) */
+} sgn_status;
+
+typedef enum { SGN_F32 = 0, SGN_F16 = 1, SGN_BF16 = 2 } sgn_dtype;   /* frame texel storage */
+typedef enum { SGN_HOST = 0, SGN_DEVICE = 1 } sgn_mem;              /* where a pointer points */
+
+/* Surfel input states (sgn_init_surfels). */
+enum { SGN_STATE_EMPTY = 0, SGN_STATE_VALID = 1, SGN_STATE_TO_SEED = 2 };
+
+/* Per-surfel result status: low 6 bits = outcome, high bits = flags. */
+enum {
+    SGN_SURFEL_OK = 0,               /* last iteration took a step (or no iterations were run) */
+    SGN_SURFEL_EMPTY = 1,            /* not a surfel */
+    SGN_SURFEL_UNSEEDED = 2,         /* TO_SEED but no VALID neighbour gave a value */
+    SGN_SURFEL_UNDERDETERMINED = 3,  /* last iteration had fewer than min_residuals valid samples */
+    SGN_SURFEL_SINGULAR = 4,         /* damped normal matrix not positive definite */
+    SGN_SURFEL_STEP_REJECTED = 5,    /* step gave id_s <= 0 or a non-finite value; kept old values */
+    SGN_SURFEL_SEEDED = 0x40,        /* parameters came from neighbour seeding */
+    SGN_SURFEL_FP64 = 0x80           /* at least one normal-equation solve ran in FP64 */
+};
+
+typedef struct {
+    int width, height;        /* keyframe and frame size, pixels; >= 8 and <= 16384 */
+    int patch;                /* P: 4, 8 or 16 */
+    int max_frames;           /* frame slots, 1..SGN_MAX_FRAMES */
+    sgn_dtype image_dtype;    /* storage of frame intensity + gradient texels */
+    float huber_k;            /* Huber threshold on intensity residuals (intensities in [0,1]); default 9/255 */
+    float lm_lambda;          /* Marquardt damping: H + lm_lambda diag(m, m, H33), m = (H11+H22)/2; default 1e-3 */
+    double fp64_cond;         /* solve in FP64 when cond2 of the Jacobi-scaled H exceeds this; <= 0: never; default 1e6 */
+    int optimize_normal;      /* 1; 0 = depth-only ablation (d id_u / d n := 0, Sec. 4.4) */
+    int min_residuals;        /* fewer valid samples than this: no update; default 8 */
+} sgn_plan_desc;
+
+typedef struct sgn_plan sgn_plan;     /* opaque, host side */
+typedef struct sgn_batch sgn_batch;   /* opaque, host side */
+
+/* Fill *desc with the defaults above for the given size. */
+sgn_status sgn_plan_desc_default(sgn_plan_desc* desc, int width, int height, int patch, int max_frames);
+
+/* Create / destroy a plan.  Creation validates desc and allocates host memory only. */
+sgn_status sgn_plan_create(const sgn_plan_desc* desc, sgn_plan** out);
+sgn_status sgn_plan_destroy(sgn_plan* plan);
+
+/* Number of surfels S = (W / P) * (H / P). */
+sgn_status sgn_plan_num_surfels(const sgn_plan* plan, int* num_surfels);
+
+/* Device workspace bytes the plan needs (256-byte aligned base required). */
+sgn_status sgn_plan_workspace_bytes(const sgn_plan* plan, size_t* bytes);
+
+/* Kernel mapping of sgn_run / sgn_solve: lanes per surfel (P=4: 8 or 16; P=8: 8, 16 or 32;
+ * P=16: 32) and threads per block (multiple of 32 in [32, 256]); 0 selects the default
+ * (P=4: 8, P=8: 16, P=16: 32 lanes; 256 threads).  Results do not depend on the mapping
+ * beyond floating-point summation order. */
+sgn_status sgn_plan_set_mapping(sgn_plan* plan, int lanes_per_surfel, int block_threads);
+
+/* Bind a device workspace (>= sgn_plan_workspace_bytes, 256-byte aligned) and a CUDA stream
+ * (cudaStream_t; NULL = legacy default stream) on the current device.  Clears the depth map.
+ * May be called again to move the plan to another workspace/stream (state is not kept). */
+sgn_status sgn_plan_bind(sgn_plan* plan, void* d_workspace, size_t bytes, void* cuda_stream);
+
+/* Pinhole intrinsics, pixels (Eq. 2: r_u = K^-1 (u_x, u_y, 1)).  fx, fy > 0, finite. */
+sgn_status sgn_set_intrinsics(sgn_plan* plan, double fx, double fy, double cx, double cy);
+
+/* Keyframe intensity I_kf (Eq. 5): W x H floats, rows pitch_bytes apart (>= 4 W). */
+sgn_status sgn_set_keyframe(sgn_plan* plan, const float* img, size_t pitch_bytes, sgn_mem mem);
+
+/* Observing frame `slot` (0 <= slot < max_frames): W x H float intensities, rows pitch_bytes
+ * apart, and its pose T_f_kf (12 doubles, row-major [R | t], keyframe -> frame, Eq. 6;
+ * R must be a rotation to 1e-6).  Enqueues the frame preparation (central-difference
+ * gradients, packed intensity+gradient texels in the plan's image_dtype). */
+sgn_status sgn_set_frame(sgn_plan* plan, int slot, const float* img, size_t pitch_bytes, sgn_mem mem,
+                         const double T_f_kf[12]);
+
+/* Frames 0..n-1 at once (one preparation launch): imgs[i] as in sgn_set_frame, poses 12 n doubles. */
+sgn_status sgn_set_frames(sgn_plan* plan, int n, const float* const* imgs, size_t pitch_bytes, sgn_mem mem,
+                          const double* T_f_kf);
+
+/* Number of frames used by the cost (Omega of Eq. 5): 1..max_frames, each must have been set. */
+sgn_status sgn_set_num_frames(sgn_plan* plan, int n);
+
+/* Initial surfels: inverse depth (S floats), unit normals (3 S floats, xyz per surfel) and
+ * states (S bytes, SGN_STATE_*).  Values of non-VALID surfels are ignored. */
+sgn_status sgn_init_surfels(sgn_plan* plan, const float* inv_depth, const float* normal, const uint8_t* state,
+                            sgn_mem mem);
+
+/* Sec. 2.3 neighbour seeding, one pass: every TO_SEED surfel takes the mean of Eq. 3 at its
+ * centre ray over its 8-connected VALID neighbours (as given to sgn_init_surfels) and the
+ * normalised sum of their camera-facing normals.  Enqueued on the stream. */
+sgn_status sgn_seed_surfels(sgn_plan* plan);
+
+/* Sec. 2.4: `iters` damped Gauss-Newton iterations on every surfel, continuing from the
+ * current state, then one evaluation at the returned parameters giving the cost (the
+ * surfel's "last residual", Sec. 2.1) and the valid-sample count; also renders the
+ * per-pixel inverse depth map (Eq. 3).  iters >= 0.  Enqueued on the stream. */
+sgn_status sgn_run(sgn_plan* plan, int iters);
+
+/* The whole path in one launch: seeding (from the initial surfels), `iters` iterations,
+ * final cost and the depth map.  Equivalent to sgn_seed_surfels + sgn_run. */
+sgn_status sgn_solve(sgn_plan* plan, int iters);
+
+/* Enqueue copies of the current surfels: inverse depth (S), normal (3 S), cost (S), valid
+ * samples (S), status (S).  Any pointer may be NULL.  Valid after sgn_sync. */
+sgn_status sgn_read_surfels(sgn_plan* plan, float* inv_depth, float* normal, float* cost, int32_t* nres,
+                            uint8_t* status, sgn_mem mem);
+
+/* Enqueue copies of the per-pixel inverse depth (W x H floats, 0 where no surfel) and the
+ * generating surfel index (W x H int32, -1 where none), tightly packed rows (Sec. 2.2). */
+sgn_status sgn_read_depth_map(sgn_plan* plan, float* inv_depth, int32_t* surfel_index, sgn_mem mem);
+
+/* Wait for the plan's stream; timeout_ns = 0 waits forever.  SGN_ERR_TIMEOUT if the
+ * deadline passes (the work keeps running), SGN_ERR_CUDA on an asynchronous error. */
+sgn_status sgn_sync(sgn_plan* plan, uint64_t timeout_ns);
+
+/* Surfel state snapshot (checkpoint/resume): bytes needed, then copy to/from host memory.
+ * Export is synchronous (the stream is synchronised).  Importing the exported bytes and
+ * running k more iterations equals running them without the snapshot, bit for bit. */
+sgn_status sgn_state_bytes(const sgn_plan* plan, size_t* bytes);
+sgn_status sgn_export_state(sgn_plan* plan, void* host, size_t bytes);
+sgn_status sgn_import_state(sgn_plan* plan, const void* host, size_t bytes);
+
+/* ---- batches: many keyframe plans in one persistent launch --------------------------- */
+
+/* A batch groups up to max_plans bound plans (any sizes, patches, frame counts, dtypes).
+ * sgn_batch_run runs, for every plan, the same work as sgn_solve, in one persistent kernel
+ * over a device work list of (plan, surfel range) items, on `cuda_stream`.  The batch needs a
+ * small device workspace of its own (sgn_batch_workspace_bytes, after adding the plans). */
+sgn_status sgn_batch_create(int max_plans, sgn_batch** out);
+sgn_status sgn_batch_add(sgn_batch* batch, sgn_plan* plan);
+sgn_status sgn_batch_clear(sgn_batch* batch);
+sgn_status sgn_batch_workspace_bytes(const sgn_batch* batch, size_t* bytes);
+sgn_status sgn_batch_bind(sgn_batch* batch, void* d_workspace, size_t bytes, void* cuda_stream);
+/* Schedule of the persistent launch: variant 0 maps P=4/8/16 surfels to 8/16/32 lanes,
+ * variant 1 to 16/32/32 lanes; chunk = surfels per work item (1..65536).  Defaults 0 and 64. */
+sgn_status sgn_batch_set_schedule(sgn_batch* batch, int variant, int chunk);
+sgn_status sgn_batch_run(sgn_batch* batch, int iters);
+sgn_status sgn_batch_sync(sgn_batch* batch, uint64_t timeout_ns);
+sgn_status sgn_batch_destroy(sgn_batch* batch);
+
+/* ---- introspection --------------------------------------------------------------------- */
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* sgn_last_error(void);
+
+/* Number of kernels libsgn has launched in this process (all plans and batches). */
+uint64_t sgn_launch_count(void);
+
+/* ABI version (SGN_ABI_VERSION). */
+int sgn_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGN_H */

@@ -1,0 +1,472 @@
+"""Python binding of libsgn: per-surfel Gauss-Newton photometric optimisation on the GPU.
+
+The binding only marshals arguments: every step of the computation runs in the CUDA kernels of
+``libsgn.so`` (built in-tree for sm_103a by ``paper_1910_01997_gb300/build.py``).  PyTorch supplies
+device memory and CUDA streams.  If the library is missing, importing this package fails.
+
+Functions carry the names of the C ABI in ``include/sgn.h``; a non-OK status raises ``SgnError``.
+``Plan`` and ``Batch`` wrap a plan/batch together with its torch-allocated workspace.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgn.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_1910_01997_gb300/build.py` "
+                      "(nvcc, sm_103a); there is no fallback implementation")
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------------------------------- constants
+SGN_OK, SGN_ERR_INVALID_ARGUMENT, SGN_ERR_NOT_BOUND, SGN_ERR_WORKSPACE_TOO_SMALL = 0, -1, -2, -3
+SGN_ERR_CUDA, SGN_ERR_TIMEOUT, SGN_ERR_ADMISSION, SGN_ERR_STATE = -4, -5, -6, -7
+SGN_F32, SGN_F16, SGN_BF16 = 0, 1, 2
+SGN_HOST, SGN_DEVICE = 0, 1
+SGN_STATE_EMPTY, SGN_STATE_VALID, SGN_STATE_TO_SEED = 0, 1, 2
+SGN_SURFEL_OK, SGN_SURFEL_EMPTY, SGN_SURFEL_UNSEEDED = 0, 1, 2
+SGN_SURFEL_UNDERDETERMINED, SGN_SURFEL_SINGULAR, SGN_SURFEL_STEP_REJECTED = 3, 4, 5
+SGN_SURFEL_SEEDED, SGN_SURFEL_FP64 = 0x40, 0x80
+SGN_MAX_FRAMES = 16
+DTYPES = {"f32": SGN_F32, "f16": SGN_F16, "bf16": SGN_BF16}
+
+
+class sgn_plan_desc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("patch", ctypes.c_int),
+                ("max_frames", ctypes.c_int), ("image_dtype", ctypes.c_int), ("huber_k", ctypes.c_float),
+                ("lm_lambda", ctypes.c_float), ("fp64_cond", ctypes.c_double), ("optimize_normal", ctypes.c_int),
+                ("min_residuals", ctypes.c_int)]
+
+
+class SgnError(RuntimeError):
+    def __init__(self, status: int, func: str):
+        self.status = status
+        msg = _lib.sgn_last_error().decode(errors="replace")
+        super().__init__(f"{func} failed with status {status}: {msg}")
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+_SIGS = {
+    "sgn_plan_desc_default": [ctypes.POINTER(sgn_plan_desc), _I, _I, _I, _I],
+    "sgn_plan_create": [ctypes.POINTER(sgn_plan_desc), ctypes.POINTER(_P)],
+    "sgn_plan_destroy": [_P],
+    "sgn_plan_num_surfels": [_P, ctypes.POINTER(_I)],
+    "sgn_plan_workspace_bytes": [_P, ctypes.POINTER(_SZ)],
+    "sgn_plan_set_mapping": [_P, _I, _I],
+    "sgn_plan_bind": [_P, _P, _SZ, _P],
+    "sgn_set_intrinsics": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double],
+    "sgn_set_keyframe": [_P, _P, _SZ, _I],
+    "sgn_set_frame": [_P, _I, _P, _SZ, _I, _P],
+    "sgn_set_frames": [_P, _I, _P, _SZ, _I, _P],
+    "sgn_set_num_frames": [_P, _I],
+    "sgn_init_surfels": [_P, _P, _P, _P, _I],
+    "sgn_seed_surfels": [_P],
+    "sgn_run": [_P, _I],
+    "sgn_solve": [_P, _I],
+    "sgn_read_surfels": [_P, _P, _P, _P, _P, _P, _I],
+    "sgn_read_depth_map": [_P, _P, _P, _I],
+    "sgn_sync": [_P, ctypes.c_uint64],
+    "sgn_state_bytes": [_P, ctypes.POINTER(_SZ)],
+    "sgn_export_state": [_P, _P, _SZ],
+    "sgn_import_state": [_P, _P, _SZ],
+    "sgn_batch_create": [_I, ctypes.POINTER(_P)],
+    "sgn_batch_add": [_P, _P],
+    "sgn_batch_clear": [_P],
+    "sgn_batch_workspace_bytes": [_P, ctypes.POINTER(_SZ)],
+    "sgn_batch_bind": [_P, _P, _SZ, _P],
+    "sgn_batch_set_schedule": [_P, _I, _I],
+    "sgn_batch_run": [_P, _I],
+    "sgn_batch_sync": [_P, ctypes.c_uint64],
+    "sgn_batch_destroy": [_P],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = ctypes.c_int
+_lib.sgn_last_error.restype = ctypes.c_char_p
+_lib.sgn_last_error.argtypes = []
+_lib.sgn_launch_count.restype = ctypes.c_uint64
+_lib.sgn_launch_count.argtypes = []
+_lib.sgn_abi_version.restype = ctypes.c_int
+_lib.sgn_abi_version.argtypes = []
+
+
+def _call(name, *args):
+    st = getattr(_lib, name)(*args)
+    if st != SGN_OK:
+        raise SgnError(st, name)
+    return st
+
+
+def _status(name, *args) -> int:
+    """Call without raising; returns the sgn_status."""
+    return getattr(_lib, name)(*args)
+
+
+# ------------------------------------------------------------------------------- C-ABI functions
+
+def sgn_plan_desc_default(width, height, patch, max_frames) -> sgn_plan_desc:
+    d = sgn_plan_desc()
+    _call("sgn_plan_desc_default", ctypes.byref(d), width, height, patch, max_frames)
+    return d
+
+
+def sgn_plan_create(desc: sgn_plan_desc) -> int:
+    h = _P()
+    _call("sgn_plan_create", ctypes.byref(desc), ctypes.byref(h))
+    return h.value
+
+
+def sgn_plan_destroy(plan):
+    _call("sgn_plan_destroy", plan)
+
+
+def sgn_plan_num_surfels(plan) -> int:
+    n = _I()
+    _call("sgn_plan_num_surfels", plan, ctypes.byref(n))
+    return n.value
+
+
+def sgn_plan_workspace_bytes(plan) -> int:
+    n = _SZ()
+    _call("sgn_plan_workspace_bytes", plan, ctypes.byref(n))
+    return n.value
+
+
+def sgn_plan_set_mapping(plan, lanes_per_surfel, block_threads):
+    _call("sgn_plan_set_mapping", plan, lanes_per_surfel, block_threads)
+
+
+def sgn_plan_bind(plan, d_workspace, nbytes, cuda_stream):
+    _call("sgn_plan_bind", plan, d_workspace, nbytes, cuda_stream)
+
+
+def sgn_set_intrinsics(plan, fx, fy, cx, cy):
+    _call("sgn_set_intrinsics", plan, fx, fy, cx, cy)
+
+
+def sgn_set_keyframe(plan, ptr, pitch_bytes, mem):
+    _call("sgn_set_keyframe", plan, ptr, pitch_bytes, mem)
+
+
+def sgn_set_frame(plan, slot, ptr, pitch_bytes, mem, pose_ptr):
+    _call("sgn_set_frame", plan, slot, ptr, pitch_bytes, mem, pose_ptr)
+
+
+def sgn_set_frames(plan, n, ptrs_ptr, pitch_bytes, mem, poses_ptr):
+    _call("sgn_set_frames", plan, n, ptrs_ptr, pitch_bytes, mem, poses_ptr)
+
+
+def sgn_set_num_frames(plan, n):
+    _call("sgn_set_num_frames", plan, n)
+
+
+def sgn_init_surfels(plan, id_ptr, n_ptr, state_ptr, mem):
+    _call("sgn_init_surfels", plan, id_ptr, n_ptr, state_ptr, mem)
+
+
+def sgn_seed_surfels(plan):
+    _call("sgn_seed_surfels", plan)
+
+
+def sgn_run(plan, iters):
+    _call("sgn_run", plan, iters)
+
+
+def sgn_solve(plan, iters):
+    _call("sgn_solve", plan, iters)
+
+
+def sgn_read_surfels(plan, id_ptr, n_ptr, cost_ptr, nres_ptr, status_ptr, mem):
+    _call("sgn_read_surfels", plan, id_ptr, n_ptr, cost_ptr, nres_ptr, status_ptr, mem)
+
+
+def sgn_read_depth_map(plan, depth_ptr, sidx_ptr, mem):
+    _call("sgn_read_depth_map", plan, depth_ptr, sidx_ptr, mem)
+
+
+def sgn_sync(plan, timeout_ns=0):
+    _call("sgn_sync", plan, timeout_ns)
+
+
+def sgn_state_bytes(plan) -> int:
+    n = _SZ()
+    _call("sgn_state_bytes", plan, ctypes.byref(n))
+    return n.value
+
+
+def sgn_export_state(plan, host_ptr, nbytes):
+    _call("sgn_export_state", plan, host_ptr, nbytes)
+
+
+def sgn_import_state(plan, host_ptr, nbytes):
+    _call("sgn_import_state", plan, host_ptr, nbytes)
+
+
+def sgn_batch_create(max_plans) -> int:
+    h = _P()
+    _call("sgn_batch_create", max_plans, ctypes.byref(h))
+    return h.value
+
+
+def sgn_batch_add(batch, plan):
+    _call("sgn_batch_add", batch, plan)
+
+
+def sgn_batch_clear(batch):
+    _call("sgn_batch_clear", batch)
+
+
+def sgn_batch_workspace_bytes(batch) -> int:
+    n = _SZ()
+    _call("sgn_batch_workspace_bytes", batch, ctypes.byref(n))
+    return n.value
+
+
+def sgn_batch_bind(batch, d_workspace, nbytes, cuda_stream):
+    _call("sgn_batch_bind", batch, d_workspace, nbytes, cuda_stream)
+
+
+def sgn_batch_set_schedule(batch, variant, chunk):
+    _call("sgn_batch_set_schedule", batch, variant, chunk)
+
+
+def sgn_batch_run(batch, iters):
+    _call("sgn_batch_run", batch, iters)
+
+
+def sgn_batch_sync(batch, timeout_ns=0):
+    _call("sgn_batch_sync", batch, timeout_ns)
+
+
+def sgn_batch_destroy(batch):
+    _call("sgn_batch_destroy", batch)
+
+
+def sgn_last_error() -> str:
+    return _lib.sgn_last_error().decode(errors="replace")
+
+
+def sgn_launch_count() -> int:
+    return int(_lib.sgn_launch_count())
+
+
+def sgn_abi_version() -> int:
+    return int(_lib.sgn_abi_version())
+
+
+# ------------------------------------------------------------------------------- helpers
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _ptr_and_mem(a):
+    """(pointer, sgn_mem, keepalive) for a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            a = np.ascontiguousarray(a)
+        return a.ctypes.data, SGN_HOST, a
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return a.data_ptr(), (SGN_DEVICE if a.is_cuda else SGN_HOST), a
+    raise TypeError(f"expected a numpy array or torch tensor, got {type(a)}")
+
+
+def _as(a, np_dtype, torch_dtype):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np_dtype)
+    return a.to(torch_dtype).contiguous()
+
+
+class Plan:
+    """A plan plus its device workspace (a torch uint8 tensor) on the current CUDA device/stream."""
+
+    def __init__(self, width, height, patch, max_frames, image_dtype="f32", *, huber_k=9.0 / 255.0,
+                 lm_lambda=1e-3, fp64_cond=1e6, optimize_normal=True, min_residuals=8, stream=None,
+                 lanes_per_surfel=0, block_threads=0):
+        torch = _torch()
+        d = sgn_plan_desc_default(width, height, patch, max_frames)
+        d.image_dtype = DTYPES[image_dtype] if isinstance(image_dtype, str) else int(image_dtype)
+        d.huber_k, d.lm_lambda, d.fp64_cond = huber_k, lm_lambda, fp64_cond
+        d.optimize_normal, d.min_residuals = int(bool(optimize_normal)), min_residuals
+        self.desc = d
+        self.handle = sgn_plan_create(d)
+        self.W, self.H, self.P = width, height, patch
+        self.S = sgn_plan_num_surfels(self.handle)
+        if lanes_per_surfel or block_threads:
+            sgn_plan_set_mapping(self.handle, lanes_per_surfel, block_threads)
+        nbytes = sgn_plan_workspace_bytes(self.handle)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        sgn_plan_bind(self.handle, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sgn_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # inputs
+    def set_intrinsics(self, fx, fy, cx, cy):
+        sgn_set_intrinsics(self.handle, float(fx), float(fy), float(cx), float(cy))
+
+    def set_keyframe(self, img):
+        img = _as(img, np.float32, _torch().float32)
+        ptr, mem, keep = _ptr_and_mem(img)
+        self._keep.append(keep)
+        sgn_set_keyframe(self.handle, ptr, self.W * 4, mem)
+
+    def set_frames(self, frames, poses):
+        """frames: (F, H, W) float32 array/tensor or a list of (H, W); poses: (F, 3, 4) keyframe->frame."""
+        torch = _torch()
+        if isinstance(frames, (list, tuple)):
+            frames = [_as(f, np.float32, torch.float32) for f in frames]
+        else:
+            frames = [_as(frames[i], np.float32, torch.float32) for i in range(len(frames))]
+        info = [_ptr_and_mem(f) for f in frames]
+        mems = {m for _, m, _ in info}
+        if len(mems) != 1:
+            raise ValueError("frames must all be host arrays or all device tensors")
+        ptrs = (ctypes.c_void_p * len(info))(*[p for p, _, _ in info])
+        T = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(len(info), 12))
+        self._keep.extend([k for _, _, k in info] + [ptrs, T])
+        sgn_set_frames(self.handle, len(info), ctypes.cast(ptrs, ctypes.c_void_p), self.W * 4, mems.pop(),
+                       T.ctypes.data)
+
+    def set_frame(self, slot, img, pose):
+        img = _as(img, np.float32, _torch().float32)
+        ptr, mem, keep = _ptr_and_mem(img)
+        T = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(12))
+        self._keep.extend([keep, T])
+        sgn_set_frame(self.handle, slot, ptr, self.W * 4, mem, T.ctypes.data)
+
+    def set_num_frames(self, n):
+        sgn_set_num_frames(self.handle, n)
+
+    def init_surfels(self, inv_depth, normal, state):
+        torch = _torch()
+        a = _as(inv_depth, np.float32, torch.float32)
+        b = _as(normal, np.float32, torch.float32)
+        c = _as(state, np.uint8, torch.uint8)
+        (pa, ma, ka), (pb, mb, kb), (pc, mc, kc) = map(_ptr_and_mem, (a, b, c))
+        if len({ma, mb, mc}) != 1:
+            raise ValueError("surfel arrays must share one memory kind")
+        self._keep.extend([ka, kb, kc])
+        sgn_init_surfels(self.handle, pa, pb, pc, ma)
+
+    # work
+    def seed(self):
+        sgn_seed_surfels(self.handle)
+
+    def run(self, iters):
+        sgn_run(self.handle, int(iters))
+
+    def solve(self, iters):
+        sgn_solve(self.handle, int(iters))
+
+    def sync(self, timeout_ns=0):
+        sgn_sync(self.handle, timeout_ns)
+        self._keep.clear()
+
+    # outputs
+    def read_surfels(self, device=False):
+        """Returns dict(id (S,), n (S, 3), cost (S,), nres (S,), status (S,)) as numpy (synchronises)
+        or, with device=True, as CUDA tensors (enqueued, no synchronisation)."""
+        torch = _torch()
+        S = self.S
+        if device:
+            out = dict(id=torch.empty(S, device="cuda"), n=torch.empty(S, 3, device="cuda"),
+                       cost=torch.empty(S, device="cuda"), nres=torch.empty(S, dtype=torch.int32, device="cuda"),
+                       status=torch.empty(S, dtype=torch.uint8, device="cuda"))
+            sgn_read_surfels(self.handle, *[out[k].data_ptr() for k in ("id", "n", "cost", "nres", "status")],
+                             SGN_DEVICE)
+            return out
+        out = dict(id=np.empty(S, np.float32), n=np.empty((S, 3), np.float32), cost=np.empty(S, np.float32),
+                   nres=np.empty(S, np.int32), status=np.empty(S, np.uint8))
+        sgn_read_surfels(self.handle, *[out[k].ctypes.data for k in ("id", "n", "cost", "nres", "status")], SGN_HOST)
+        self.sync()
+        return out
+
+    def read_depth_map(self):
+        inv = np.empty((self.H, self.W), np.float32)
+        sidx = np.empty((self.H, self.W), np.int32)
+        sgn_read_depth_map(self.handle, inv.ctypes.data, sidx.ctypes.data, SGN_HOST)
+        self.sync()
+        return inv, sidx
+
+    def export_state(self) -> bytes:
+        n = sgn_state_bytes(self.handle)
+        buf = ctypes.create_string_buffer(n)
+        sgn_export_state(self.handle, ctypes.addressof(buf), n)
+        return buf.raw
+
+    def import_state(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        sgn_import_state(self.handle, ctypes.addressof(buf), len(data))
+
+
+class Batch:
+    """A batch of bound plans run by one persistent, graph-captured launch."""
+
+    def __init__(self, max_plans, stream=None):
+        self.handle = sgn_batch_create(max_plans)
+        self.plans = []
+        self.workspace = None
+        self.stream = stream if stream is not None else _torch().cuda.current_stream()
+
+    def add(self, plan: Plan):
+        sgn_batch_add(self.handle, plan.handle)
+        self.plans.append(plan)
+        self.workspace = None
+
+    def clear(self):
+        sgn_batch_clear(self.handle)
+        self.plans = []
+        self.workspace = None
+
+    def set_schedule(self, variant, chunk):
+        sgn_batch_set_schedule(self.handle, variant, chunk)
+        self.workspace = None
+
+    def _bind(self):
+        torch = _torch()
+        n = sgn_batch_workspace_bytes(self.handle)
+        self.workspace = torch.empty(n, dtype=torch.uint8, device="cuda")
+        sgn_batch_bind(self.handle, self.workspace.data_ptr(), n, self.stream.cuda_stream)
+
+    def run(self, iters):
+        if self.workspace is None or self.workspace.numel() < sgn_batch_workspace_bytes(self.handle):
+            self._bind()
+        sgn_batch_run(self.handle, int(iters))
+
+    def sync(self, timeout_ns=0):
+        sgn_batch_sync(self.handle, timeout_ns)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sgn_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

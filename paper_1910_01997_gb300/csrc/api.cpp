@@ -1,0 +1,870 @@
+// Host runtime behind the C ABI of include/sgn.h: argument validation, workspace layout, uploads,
+// kernel launches, synchronisation, checkpoints and batches.  No device memory is allocated here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sgn.h"
+#include "sgn_internal.h"
+
+using sgn::PlanParams;
+using sgn::WorkItem;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+
+sgn_status fail(sgn_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+sgn_status cuda_fail(int err, const char* what) {
+    return fail(SGN_ERR_CUDA, "%s: %s", what, cudaGetErrorString(static_cast<cudaError_t>(err)));
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Makes the plan's device current for the duration of a call and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (dev < 0) return;
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct Layout {
+    size_t kf, tex, raw, id0, n0, state0, id, n, cost, nres, status, depth, sidx, total;
+    int kf_pitch, tex_pitch, raw_pitch;
+    long long tex_plane, raw_plane;
+};
+
+Layout make_layout(const sgn_plan_desc& d, int S) {
+    Layout L{};
+    const size_t W = size_t(d.width), H = size_t(d.height);
+    L.kf_pitch = int(round_up(W, 64));
+    L.tex_pitch = int(round_up(W, 32));
+    L.raw_pitch = int(round_up(W, 64));
+    L.tex_plane = (long long)H * L.tex_pitch;
+    L.raw_plane = (long long)H * L.raw_pitch;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = round_up(off + bytes, sgn::kAlign);
+        return o;
+    };
+    L.kf = take(H * L.kf_pitch * sizeof(float));
+    L.tex = take(size_t(d.max_frames) * L.tex_plane * sgn::texel_bytes(d.image_dtype));
+    L.raw = take(size_t(d.max_frames) * L.raw_plane * sizeof(float));
+    L.id0 = take(size_t(S) * sizeof(float));
+    L.n0 = take(size_t(S) * 3 * sizeof(float));
+    L.state0 = take(size_t(S));
+    L.id = take(size_t(S) * sizeof(float));
+    L.n = take(size_t(S) * 3 * sizeof(float));
+    L.cost = take(size_t(S) * sizeof(float));
+    L.nres = take(size_t(S) * sizeof(int32_t));
+    L.status = take(size_t(S));
+    L.depth = take(W * H * sizeof(float));
+    L.sidx = take(W * H * sizeof(int32_t));
+    L.total = off;
+    return L;
+}
+
+bool finite_all(const double* v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+sgn_status check_pose(const double* T) {
+    if (!T) return fail(SGN_ERR_INVALID_ARGUMENT, "pose pointer is NULL");
+    if (!finite_all(T, 12)) return fail(SGN_ERR_INVALID_ARGUMENT, "pose has non-finite entries");
+    double worst = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double d = 0.0;
+            for (int k = 0; k < 3; ++k) d += T[4 * k + i] * T[4 * k + j];
+            worst = std::max(worst, std::fabs(d - (i == j ? 1.0 : 0.0)));
+        }
+    const double det = T[0] * (T[5] * T[10] - T[6] * T[9]) - T[1] * (T[4] * T[10] - T[6] * T[8]) +
+                       T[2] * (T[4] * T[9] - T[5] * T[8]);
+    if (worst > 1e-6 || det <= 0.0) return fail(SGN_ERR_INVALID_ARGUMENT, "pose rotation is not a rotation (|R^T R - I| = %g, det = %g)", worst, det);
+    return SGN_OK;
+}
+
+}  // namespace
+
+namespace sgn {
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace sgn
+
+struct sgn_plan {
+    sgn_plan_desc desc{};
+    int TX = 0, TY = 0, S = 0;
+    Layout L{};
+    bool have_K = false;
+    double fx = 0, fy = 0, cx = 0, cy = 0;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    int device = -1;
+    cudaEvent_t done = nullptr;
+    bool kf_set = false;
+    bool frame_set[sgn::kMaxFrames] = {};
+    double T[sgn::kMaxFrames][12] = {};
+    int F = 0;
+    bool surfels_set = false;
+    bool depth_valid = false;
+    int lanes = 0, block = 256;
+};
+
+struct sgn_batch {
+    int max_plans = 0;
+    std::vector<sgn_plan*> plans;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    int device = -1;
+    int variant = 0;
+    int chunk = 64;
+    bool dirty = true;
+    int n_items = 0;
+    std::vector<PlanParams> h_plans;
+    std::vector<WorkItem> h_items;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_iters = -1;
+    int graph_grid = 0;
+    cudaEvent_t done = nullptr;
+    std::vector<cudaEvent_t> plan_events;
+};
+
+namespace {
+
+int default_lanes(int P) { return P == 4 ? 8 : (P == 8 ? 16 : 32); }
+
+bool mapping_supported(int P, int G) {
+    return (P == 4 && (G == 8 || G == 16)) || (P == 8 && (G == 8 || G == 16 || G == 32)) || (P == 16 && G == 32);
+}
+
+PlanParams make_params(const sgn_plan* p) {
+    PlanParams pp{};
+    const sgn_plan_desc& d = p->desc;
+    pp.W = d.width;
+    pp.H = d.height;
+    pp.P = d.patch;
+    pp.TX = p->TX;
+    pp.TY = p->TY;
+    pp.S = p->S;
+    pp.F = p->F;
+    pp.dtype = d.image_dtype;
+    pp.fx = float(p->fx);
+    pp.fy = float(p->fy);
+    pp.cx = float(p->cx);
+    pp.cy = float(p->cy);
+    pp.ifx = float(1.0 / p->fx);
+    pp.ify = float(1.0 / p->fy);
+    pp.huber_k = d.huber_k;
+    pp.lm_lambda = d.lm_lambda;
+    pp.fp64_cond = d.fp64_cond > 0 ? float(std::min(d.fp64_cond, 3.0e38)) : 0.0f;
+    pp.optimize_normal = d.optimize_normal;
+    pp.min_residuals = d.min_residuals;
+    char* b = p->ws;
+    const Layout& L = p->L;
+    pp.kf = reinterpret_cast<const float*>(b + L.kf);
+    pp.kf_pitch = L.kf_pitch;
+    pp.tex = b + L.tex;
+    pp.tex_pitch = L.tex_pitch;
+    pp.tex_plane = L.tex_plane;
+    pp.id0 = reinterpret_cast<const float*>(b + L.id0);
+    pp.n0 = reinterpret_cast<const float*>(b + L.n0);
+    pp.state0 = reinterpret_cast<const uint8_t*>(b + L.state0);
+    pp.id = reinterpret_cast<float*>(b + L.id);
+    pp.n = reinterpret_cast<float*>(b + L.n);
+    pp.cost = reinterpret_cast<float*>(b + L.cost);
+    pp.nres = reinterpret_cast<int32_t*>(b + L.nres);
+    pp.status = reinterpret_cast<uint8_t*>(b + L.status);
+    pp.depth = reinterpret_cast<float*>(b + L.depth);
+    pp.sidx = reinterpret_cast<int32_t*>(b + L.sidx);
+    // Eq. 6 in homogeneous pixel coordinates: M = K R K^-1, b = K t (computed in double).
+    const double K[9] = {p->fx, 0, p->cx, 0, p->fy, p->cy, 0, 0, 1};
+    const double Ki[9] = {1.0 / p->fx, 0, -p->cx / p->fx, 0, 1.0 / p->fy, -p->cy / p->fy, 0, 0, 1};
+    for (int f = 0; f < p->F; ++f) {
+        const double* T = p->T[f];
+        double KR[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double v = 0.0;
+                for (int k = 0; k < 3; ++k) v += K[3 * i + k] * T[4 * k + j];
+                KR[3 * i + j] = v;
+            }
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) {
+                double v = 0.0;
+                for (int k = 0; k < 3; ++k) v += KR[3 * i + k] * Ki[3 * k + j];
+                pp.frames[f].M[3 * i + j] = float(v);
+            }
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) v += K[3 * i + k] * T[4 * k + 3];
+            pp.frames[f].b[i] = float(v);
+        }
+    }
+    return pp;
+}
+
+sgn_status require_bound(const sgn_plan* p) {
+    if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "plan is NULL");
+    if (!p->ws) return fail(SGN_ERR_NOT_BOUND, "plan has no workspace; call sgn_plan_bind first");
+    return SGN_OK;
+}
+
+sgn_status require_ready(const sgn_plan* p) {
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    if (!p->have_K) return fail(SGN_ERR_STATE, "intrinsics not set");
+    if (!p->kf_set) return fail(SGN_ERR_STATE, "keyframe not set");
+    if (p->F < 1) return fail(SGN_ERR_STATE, "no frames in use; call sgn_set_frame(s) / sgn_set_num_frames");
+    for (int f = 0; f < p->F; ++f)
+        if (!p->frame_set[f]) return fail(SGN_ERR_STATE, "frame slot %d in use but not set", f);
+    if (!p->surfels_set) return fail(SGN_ERR_STATE, "surfels not initialised");
+    return SGN_OK;
+}
+
+cudaMemcpyKind kind_to_device(sgn_mem m) { return m == SGN_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+cudaMemcpyKind kind_from_device(sgn_mem m) { return m == SGN_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+
+sgn_status sync_event(cudaEvent_t ev, cudaStream_t stream, uint64_t timeout_ns) {
+    cudaError_t e = cudaEventRecord(ev, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    const auto t0 = std::chrono::steady_clock::now();
+    for (unsigned spin = 0;; ++spin) {
+        e = cudaEventQuery(ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "asynchronous CUDA error");
+        if (timeout_ns) {
+            const auto dt = std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0);
+            if (uint64_t(dt.count()) >= timeout_ns) return fail(SGN_ERR_TIMEOUT, "sync deadline passed");
+        }
+        if (spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "CUDA error");
+    return SGN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sgn_status sgn_plan_desc_default(sgn_plan_desc* d, int width, int height, int patch, int max_frames) {
+    if (!d) return fail(SGN_ERR_INVALID_ARGUMENT, "desc is NULL");
+    std::memset(d, 0, sizeof *d);
+    d->width = width;
+    d->height = height;
+    d->patch = patch;
+    d->max_frames = max_frames;
+    d->image_dtype = SGN_F32;
+    d->huber_k = 9.0f / 255.0f;
+    d->lm_lambda = 1e-3f;
+    d->fp64_cond = 1e6;
+    d->optimize_normal = 1;
+    d->min_residuals = 8;
+    return SGN_OK;
+}
+
+sgn_status sgn_plan_create(const sgn_plan_desc* d, sgn_plan** out) {
+    if (!d || !out) return fail(SGN_ERR_INVALID_ARGUMENT, "desc/out is NULL");
+    *out = nullptr;
+    if (d->patch != 4 && d->patch != 8 && d->patch != 16) return fail(SGN_ERR_INVALID_ARGUMENT, "patch must be 4, 8 or 16 (got %d)", d->patch);
+    if (d->width < 8 || d->height < 8 || d->width > 16384 || d->height > 16384)
+        return fail(SGN_ERR_INVALID_ARGUMENT, "image size %dx%d outside [8, 16384]", d->width, d->height);
+    if (d->width < d->patch || d->height < d->patch) return fail(SGN_ERR_INVALID_ARGUMENT, "image smaller than one tile");
+    if (d->max_frames < 1 || d->max_frames > SGN_MAX_FRAMES)
+        return fail(SGN_ERR_INVALID_ARGUMENT, "max_frames must be in [1, %d]", SGN_MAX_FRAMES);
+    if (d->image_dtype != SGN_F32 && d->image_dtype != SGN_F16 && d->image_dtype != SGN_BF16)
+        return fail(SGN_ERR_INVALID_ARGUMENT, "unknown image dtype %d", int(d->image_dtype));
+    if (!(d->huber_k > 0.0f) || !std::isfinite(d->huber_k)) return fail(SGN_ERR_INVALID_ARGUMENT, "huber_k must be positive and finite");
+    if (!(d->lm_lambda >= 0.0f) || !std::isfinite(d->lm_lambda)) return fail(SGN_ERR_INVALID_ARGUMENT, "lm_lambda must be >= 0 and finite");
+    if (std::isnan(d->fp64_cond)) return fail(SGN_ERR_INVALID_ARGUMENT, "fp64_cond is NaN");
+    if (d->optimize_normal != 0 && d->optimize_normal != 1) return fail(SGN_ERR_INVALID_ARGUMENT, "optimize_normal must be 0 or 1");
+    if (d->min_residuals < 0) return fail(SGN_ERR_INVALID_ARGUMENT, "min_residuals must be >= 0");
+    sgn_plan* p = new (std::nothrow) sgn_plan();
+    if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "out of host memory");
+    p->desc = *d;
+    p->TX = d->width / d->patch;
+    p->TY = d->height / d->patch;
+    p->S = p->TX * p->TY;
+    p->L = make_layout(*d, p->S);
+    p->lanes = default_lanes(d->patch);
+    *out = p;
+    return SGN_OK;
+}
+
+sgn_status sgn_plan_destroy(sgn_plan* p) {
+    if (!p) return SGN_OK;
+    if (p->done) {
+        DeviceGuard g(p->device);
+        cudaEventDestroy(p->done);
+    }
+    delete p;
+    return SGN_OK;
+}
+
+sgn_status sgn_plan_num_surfels(const sgn_plan* p, int* n) {
+    if (!p || !n) return fail(SGN_ERR_INVALID_ARGUMENT, "plan/out is NULL");
+    *n = p->S;
+    return SGN_OK;
+}
+
+sgn_status sgn_plan_workspace_bytes(const sgn_plan* p, size_t* bytes) {
+    if (!p || !bytes) return fail(SGN_ERR_INVALID_ARGUMENT, "plan/out is NULL");
+    *bytes = p->L.total;
+    return SGN_OK;
+}
+
+sgn_status sgn_plan_set_mapping(sgn_plan* p, int lanes_per_surfel, int block_threads) {
+    if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "plan is NULL");
+    const int G = lanes_per_surfel ? lanes_per_surfel : default_lanes(p->desc.patch);
+    const int B = block_threads ? block_threads : 256;
+    if (!mapping_supported(p->desc.patch, G)) return fail(SGN_ERR_INVALID_ARGUMENT, "%d lanes per surfel not supported for %dx%d tiles", G, p->desc.patch, p->desc.patch);
+    if (B < 32 || B > 256 || B % 32) return fail(SGN_ERR_INVALID_ARGUMENT, "block_threads must be a multiple of 32 in [32, 256]");
+    p->lanes = G;
+    p->block = B;
+    return SGN_OK;
+}
+
+sgn_status sgn_plan_bind(sgn_plan* p, void* ws, size_t bytes, void* stream) {
+    if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "plan is NULL");
+    if (!ws) return fail(SGN_ERR_INVALID_ARGUMENT, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % sgn::kAlign) return fail(SGN_ERR_INVALID_ARGUMENT, "workspace must be 256-byte aligned");
+    if (bytes < p->L.total) return fail(SGN_ERR_WORKSPACE_TOO_SMALL, "workspace %zu bytes < %zu needed", bytes, p->L.total);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaPointerAttributes attr{};
+    e = cudaPointerGetAttributes(&attr, ws);
+    if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(SGN_ERR_INVALID_ARGUMENT, "workspace is not device memory");
+    }
+    if (attr.device != dev) return fail(SGN_ERR_INVALID_ARGUMENT, "workspace is on device %d, current device is %d", attr.device, dev);
+    if (p->done && p->device != dev) {
+        DeviceGuard g(p->device);
+        cudaEventDestroy(p->done);
+        p->done = nullptr;
+    }
+    if (!p->done) {
+        e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
+    p->ws = static_cast<char*>(ws);
+    p->ws_bytes = bytes;
+    p->stream = static_cast<cudaStream_t>(stream);
+    p->device = dev;
+    p->kf_set = false;
+    p->surfels_set = false;
+    for (bool& b : p->frame_set) b = false;
+    p->F = 0;
+    const size_t npx = size_t(p->desc.width) * p->desc.height;
+    e = cudaMemsetAsync(p->ws + p->L.depth, 0, npx * sizeof(float), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->ws + p->L.sidx, 0xff, npx * sizeof(int32_t), p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the depth map");
+    p->depth_valid = true;
+    return SGN_OK;
+}
+
+sgn_status sgn_set_intrinsics(sgn_plan* p, double fx, double fy, double cx, double cy) {
+    if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "plan is NULL");
+    if (!(fx > 0) || !(fy > 0) || !std::isfinite(fx) || !std::isfinite(fy) || !std::isfinite(cx) || !std::isfinite(cy))
+        return fail(SGN_ERR_INVALID_ARGUMENT, "intrinsics must be finite with fx, fy > 0");
+    p->fx = fx;
+    p->fy = fy;
+    p->cx = cx;
+    p->cy = cy;
+    p->have_K = true;
+    return SGN_OK;
+}
+
+sgn_status sgn_set_keyframe(sgn_plan* p, const float* img, size_t pitch, sgn_mem mem) {
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    const int W = p->desc.width, H = p->desc.height;
+    if (!img) return fail(SGN_ERR_INVALID_ARGUMENT, "keyframe pointer is NULL");
+    if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
+    if (pitch < size_t(W) * sizeof(float) || pitch % sizeof(float)) return fail(SGN_ERR_INVALID_ARGUMENT, "keyframe pitch %zu invalid for width %d", pitch, W);
+    DeviceGuard g(p->device);
+    cudaError_t e = cudaMemcpy2DAsync(p->ws + p->L.kf, size_t(p->L.kf_pitch) * sizeof(float), img, pitch,
+                                      size_t(W) * sizeof(float), H, kind_to_device(mem), p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "keyframe upload");
+    p->kf_set = true;
+    return SGN_OK;
+}
+
+sgn_status sgn_set_frames(sgn_plan* p, int n, const float* const* imgs, size_t pitch, sgn_mem mem, const double* T) {
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    const int W = p->desc.width, H = p->desc.height;
+    if (n < 1 || n > p->desc.max_frames) return fail(SGN_ERR_INVALID_ARGUMENT, "frame count %d outside [1, %d]", n, p->desc.max_frames);
+    if (!imgs || !T) return fail(SGN_ERR_INVALID_ARGUMENT, "images/poses pointer is NULL");
+    if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
+    if (pitch < size_t(W) * sizeof(float) || pitch % sizeof(float)) return fail(SGN_ERR_INVALID_ARGUMENT, "frame pitch %zu invalid for width %d", pitch, W);
+    for (int i = 0; i < n; ++i) {
+        if (!imgs[i]) return fail(SGN_ERR_INVALID_ARGUMENT, "frame %d pointer is NULL", i);
+        if ((st = check_pose(T + 12 * i)) != SGN_OK) return st;
+    }
+    DeviceGuard g(p->device);
+    const float* src[sgn::kMaxFrames];
+    size_t sp[sgn::kMaxFrames];
+    for (int i = 0; i < n; ++i) {
+        if (mem == SGN_HOST) {
+            char* dst = p->ws + p->L.raw + size_t(i) * p->L.raw_plane * sizeof(float);
+            cudaError_t e = cudaMemcpy2DAsync(dst, size_t(p->L.raw_pitch) * sizeof(float), imgs[i], pitch,
+                                              size_t(W) * sizeof(float), H, cudaMemcpyHostToDevice, p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "frame upload");
+            src[i] = reinterpret_cast<const float*>(dst);
+            sp[i] = size_t(p->L.raw_pitch);
+        } else {
+            src[i] = imgs[i];
+            sp[i] = pitch / sizeof(float);
+        }
+    }
+    PlanParams pp = make_params(p);
+    int e = sgn::launch_prep_frames(pp, src, sp, 0, n, p->stream);
+    if (e) return cuda_fail(e, "frame preparation launch");
+    sgn::count_launch();
+    for (int i = 0; i < n; ++i) {
+        std::memcpy(p->T[i], T + 12 * i, sizeof(double) * 12);
+        p->frame_set[i] = true;
+    }
+    p->F = n;
+    return SGN_OK;
+}
+
+sgn_status sgn_set_frame(sgn_plan* p, int slot, const float* img, size_t pitch, sgn_mem mem, const double* T) {
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    const int W = p->desc.width, H = p->desc.height;
+    if (slot < 0 || slot >= p->desc.max_frames) return fail(SGN_ERR_INVALID_ARGUMENT, "slot %d outside [0, %d)", slot, p->desc.max_frames);
+    if (!img) return fail(SGN_ERR_INVALID_ARGUMENT, "frame pointer is NULL");
+    if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
+    if (pitch < size_t(W) * sizeof(float) || pitch % sizeof(float)) return fail(SGN_ERR_INVALID_ARGUMENT, "frame pitch %zu invalid for width %d", pitch, W);
+    if ((st = check_pose(T)) != SGN_OK) return st;
+    DeviceGuard g(p->device);
+    const float* src = img;
+    size_t sp = pitch / sizeof(float);
+    if (mem == SGN_HOST) {
+        char* dst = p->ws + p->L.raw + size_t(slot) * p->L.raw_plane * sizeof(float);
+        cudaError_t e = cudaMemcpy2DAsync(dst, size_t(p->L.raw_pitch) * sizeof(float), img, pitch, size_t(W) * sizeof(float),
+                                          H, cudaMemcpyHostToDevice, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "frame upload");
+        src = reinterpret_cast<const float*>(dst);
+        sp = size_t(p->L.raw_pitch);
+    }
+    PlanParams pp = make_params(p);
+    int e = sgn::launch_prep_frames(pp, &src, &sp, slot, 1, p->stream);
+    if (e) return cuda_fail(e, "frame preparation launch");
+    sgn::count_launch();
+    std::memcpy(p->T[slot], T, sizeof(double) * 12);
+    p->frame_set[slot] = true;
+    if (slot + 1 > p->F) p->F = slot + 1;
+    return SGN_OK;
+}
+
+sgn_status sgn_set_num_frames(sgn_plan* p, int n) {
+    if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "plan is NULL");
+    if (n < 1 || n > p->desc.max_frames) return fail(SGN_ERR_INVALID_ARGUMENT, "frame count %d outside [1, %d]", n, p->desc.max_frames);
+    for (int f = 0; f < n; ++f)
+        if (!p->frame_set[f]) return fail(SGN_ERR_STATE, "frame slot %d not set", f);
+    p->F = n;
+    return SGN_OK;
+}
+
+sgn_status sgn_init_surfels(sgn_plan* p, const float* id, const float* n, const uint8_t* state, sgn_mem mem) {
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    if (!id || !n || !state) return fail(SGN_ERR_INVALID_ARGUMENT, "surfel pointer is NULL");
+    if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
+    const size_t S = size_t(p->S);
+    if (mem == SGN_HOST) {
+        for (size_t s = 0; s < S; ++s) {
+            if (state[s] > SGN_STATE_TO_SEED) return fail(SGN_ERR_INVALID_ARGUMENT, "surfel %zu has unknown state %d", s, int(state[s]));
+            if (state[s] == SGN_STATE_VALID) {
+                const float nn = n[3 * s] * n[3 * s] + n[3 * s + 1] * n[3 * s + 1] + n[3 * s + 2] * n[3 * s + 2];
+                if (!(id[s] > 0.0f) || !std::isfinite(id[s]) || !(std::fabs(nn - 1.0f) < 1e-3f))
+                    return fail(SGN_ERR_INVALID_ARGUMENT, "valid surfel %zu needs a positive finite inverse depth and a unit normal", s);
+            }
+        }
+    }
+    DeviceGuard g(p->device);
+    const cudaMemcpyKind k = kind_to_device(mem);
+    cudaError_t e = cudaMemcpyAsync(p->ws + p->L.id0, id, S * sizeof(float), k, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.n0, n, 3 * S * sizeof(float), k, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.state0, state, S, k, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "surfel upload");
+    PlanParams pp = make_params(p);
+    int le = sgn::launch_init_state(pp, p->stream);
+    if (le) return cuda_fail(le, "surfel initialisation launch");
+    sgn::count_launch();
+    p->surfels_set = true;
+    p->depth_valid = false;
+    return SGN_OK;
+}
+
+sgn_status sgn_seed_surfels(sgn_plan* p) {
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    if (!p->have_K) return fail(SGN_ERR_STATE, "intrinsics not set");
+    if (!p->surfels_set) return fail(SGN_ERR_STATE, "surfels not initialised");
+    DeviceGuard g(p->device);
+    PlanParams pp = make_params(p);
+    int e = sgn::launch_seed(pp, p->stream);
+    if (e) return cuda_fail(e, "seeding launch");
+    sgn::count_launch();
+    p->depth_valid = false;
+    return SGN_OK;
+}
+
+static sgn_status run_mode(sgn_plan* p, int iters, int mode) {
+    sgn_status st = require_ready(p);
+    if (st != SGN_OK) return st;
+    if (iters < 0 || iters > 100000) return fail(SGN_ERR_INVALID_ARGUMENT, "iters %d outside [0, 100000]", iters);
+    DeviceGuard g(p->device);
+    PlanParams pp = make_params(p);
+    int e = sgn::launch_gn(pp, iters, mode, p->lanes, p->block, p->stream);
+    if (e) return cuda_fail(e, "Gauss-Newton launch");
+    sgn::count_launch();
+    p->depth_valid = true;
+    return SGN_OK;
+}
+
+sgn_status sgn_run(sgn_plan* p, int iters) { return run_mode(p, iters, sgn::kModeRun); }
+sgn_status sgn_solve(sgn_plan* p, int iters) { return run_mode(p, iters, sgn::kModeSolve); }
+
+sgn_status sgn_read_surfels(sgn_plan* p, float* id, float* n, float* cost, int32_t* nres, uint8_t* status, sgn_mem mem) {
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    if (!p->surfels_set) return fail(SGN_ERR_STATE, "surfels not initialised");
+    if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
+    DeviceGuard g(p->device);
+    const size_t S = size_t(p->S);
+    const cudaMemcpyKind k = kind_from_device(mem);
+    cudaError_t e = cudaSuccess;
+    if (id && e == cudaSuccess) e = cudaMemcpyAsync(id, p->ws + p->L.id, S * sizeof(float), k, p->stream);
+    if (n && e == cudaSuccess) e = cudaMemcpyAsync(n, p->ws + p->L.n, 3 * S * sizeof(float), k, p->stream);
+    if (cost && e == cudaSuccess) e = cudaMemcpyAsync(cost, p->ws + p->L.cost, S * sizeof(float), k, p->stream);
+    if (nres && e == cudaSuccess) e = cudaMemcpyAsync(nres, p->ws + p->L.nres, S * sizeof(int32_t), k, p->stream);
+    if (status && e == cudaSuccess) e = cudaMemcpyAsync(status, p->ws + p->L.status, S, k, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "surfel readback");
+    return SGN_OK;
+}
+
+sgn_status sgn_read_depth_map(sgn_plan* p, float* inv_depth, int32_t* sidx, sgn_mem mem) {
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
+    DeviceGuard g(p->device);
+    if (!p->depth_valid) {
+        if (!p->have_K || !p->surfels_set) return fail(SGN_ERR_STATE, "depth map needs intrinsics and surfels");
+        PlanParams pp = make_params(p);
+        int e = sgn::launch_render_depth(pp, p->stream);
+        if (e) return cuda_fail(e, "depth render launch");
+        sgn::count_launch();
+        p->depth_valid = true;
+    }
+    const size_t npx = size_t(p->desc.width) * p->desc.height;
+    const cudaMemcpyKind k = kind_from_device(mem);
+    cudaError_t e = cudaSuccess;
+    if (inv_depth) e = cudaMemcpyAsync(inv_depth, p->ws + p->L.depth, npx * sizeof(float), k, p->stream);
+    if (sidx && e == cudaSuccess) e = cudaMemcpyAsync(sidx, p->ws + p->L.sidx, npx * sizeof(int32_t), k, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "depth map readback");
+    return SGN_OK;
+}
+
+sgn_status sgn_sync(sgn_plan* p, uint64_t timeout_ns) {
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    DeviceGuard g(p->device);
+    return sync_event(p->done, p->stream, timeout_ns);
+}
+
+sgn_status sgn_state_bytes(const sgn_plan* p, size_t* bytes) {
+    if (!p || !bytes) return fail(SGN_ERR_INVALID_ARGUMENT, "plan/out is NULL");
+    *bytes = size_t(p->S) * (sizeof(float) * 5 + sizeof(int32_t) + 1);
+    return SGN_OK;
+}
+
+sgn_status sgn_export_state(sgn_plan* p, void* host, size_t bytes) {
+    size_t need = 0;
+    sgn_state_bytes(p, &need);
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    if (!host || bytes < need) return fail(SGN_ERR_INVALID_ARGUMENT, "state buffer NULL or smaller than %zu bytes", need);
+    char* h = static_cast<char*>(host);
+    const size_t S = size_t(p->S);
+    if ((st = sgn_read_surfels(p, reinterpret_cast<float*>(h), reinterpret_cast<float*>(h + 4 * S),
+                               reinterpret_cast<float*>(h + 16 * S), reinterpret_cast<int32_t*>(h + 20 * S),
+                               reinterpret_cast<uint8_t*>(h + 24 * S), SGN_HOST)) != SGN_OK)
+        return st;
+    return sgn_sync(p, 0);
+}
+
+sgn_status sgn_import_state(sgn_plan* p, const void* host, size_t bytes) {
+    size_t need = 0;
+    sgn_state_bytes(p, &need);
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    if (!host || bytes < need) return fail(SGN_ERR_INVALID_ARGUMENT, "state buffer NULL or smaller than %zu bytes", need);
+    DeviceGuard g(p->device);
+    const char* h = static_cast<const char*>(host);
+    const size_t S = size_t(p->S);
+    const cudaMemcpyKind k = cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(p->ws + p->L.id, h, 4 * S, k, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.n, h + 4 * S, 12 * S, k, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.cost, h + 16 * S, 4 * S, k, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.nres, h + 20 * S, 4 * S, k, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.status, h + 24 * S, S, k, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "state import");
+    p->surfels_set = true;
+    p->depth_valid = false;
+    return sgn_sync(p, 0);
+}
+
+// ------------------------------------------------------------------------------------------ batches
+
+sgn_status sgn_batch_create(int max_plans, sgn_batch** out) {
+    if (!out) return fail(SGN_ERR_INVALID_ARGUMENT, "out is NULL");
+    *out = nullptr;
+    if (max_plans < 1 || max_plans > 65536) return fail(SGN_ERR_INVALID_ARGUMENT, "max_plans outside [1, 65536]");
+    sgn_batch* b = new (std::nothrow) sgn_batch();
+    if (!b) return fail(SGN_ERR_INVALID_ARGUMENT, "out of host memory");
+    b->max_plans = max_plans;
+    *out = b;
+    return SGN_OK;
+}
+
+static void batch_drop_graph(sgn_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_iters = -1;
+}
+
+sgn_status sgn_batch_add(sgn_batch* b, sgn_plan* p) {
+    if (!b || !p) return fail(SGN_ERR_INVALID_ARGUMENT, "batch/plan is NULL");
+    if (int(b->plans.size()) >= b->max_plans) return fail(SGN_ERR_INVALID_ARGUMENT, "batch is full (%d plans)", b->max_plans);
+    b->plans.push_back(p);
+    b->dirty = true;
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_clear(sgn_batch* b) {
+    if (!b) return fail(SGN_ERR_INVALID_ARGUMENT, "batch is NULL");
+    b->plans.clear();
+    b->dirty = true;
+    return SGN_OK;
+}
+
+static size_t batch_items_upper(const sgn_batch* b) {
+    size_t n = 0;
+    for (const sgn_plan* p : b->plans) n += (size_t(p->S) + b->chunk - 1) / b->chunk;
+    return n;
+}
+
+static size_t batch_ws_need(const sgn_batch* b, size_t* off_items, size_t* off_counter) {
+    const size_t tbl = round_up(size_t(b->max_plans) * sizeof(PlanParams), sgn::kAlign);
+    const size_t items = round_up(std::max<size_t>(1, batch_items_upper(b)) * sizeof(WorkItem), sgn::kAlign);
+    if (off_items) *off_items = tbl;
+    if (off_counter) *off_counter = tbl + items;
+    return tbl + items + sgn::kAlign;
+}
+
+sgn_status sgn_batch_workspace_bytes(const sgn_batch* b, size_t* bytes) {
+    if (!b || !bytes) return fail(SGN_ERR_INVALID_ARGUMENT, "batch/out is NULL");
+    *bytes = batch_ws_need(b, nullptr, nullptr);
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_set_schedule(sgn_batch* b, int variant, int chunk) {
+    if (!b) return fail(SGN_ERR_INVALID_ARGUMENT, "batch is NULL");
+    if (variant != 0 && variant != 1) return fail(SGN_ERR_INVALID_ARGUMENT, "variant must be 0 or 1");
+    if (chunk < 1 || chunk > 65536) return fail(SGN_ERR_INVALID_ARGUMENT, "chunk outside [1, 65536]");
+    if (b->variant != variant || b->chunk != chunk) {
+        b->variant = variant;
+        b->chunk = chunk;
+        b->dirty = true;
+        batch_drop_graph(b);
+    }
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_bind(sgn_batch* b, void* ws, size_t bytes, void* stream) {
+    if (!b || !ws) return fail(SGN_ERR_INVALID_ARGUMENT, "batch/workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % sgn::kAlign) return fail(SGN_ERR_INVALID_ARGUMENT, "workspace must be 256-byte aligned");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (!b->done) {
+        e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
+    batch_drop_graph(b);
+    b->ws = static_cast<char*>(ws);
+    b->ws_bytes = bytes;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->device = dev;
+    b->dirty = true;
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_run(sgn_batch* b, int iters) {
+    if (!b) return fail(SGN_ERR_INVALID_ARGUMENT, "batch is NULL");
+    if (!b->ws) return fail(SGN_ERR_NOT_BOUND, "batch has no workspace; call sgn_batch_bind");
+    if (b->plans.empty()) return fail(SGN_ERR_STATE, "batch has no plans");
+    if (iters < 0 || iters > 100000) return fail(SGN_ERR_INVALID_ARGUMENT, "iters %d outside [0, 100000]", iters);
+    size_t off_items = 0, off_counter = 0;
+    const size_t need = batch_ws_need(b, &off_items, &off_counter);
+    if (b->ws_bytes < need) return fail(SGN_ERR_WORKSPACE_TOO_SMALL, "batch workspace %zu bytes < %zu needed", b->ws_bytes, need);
+    for (sgn_plan* p : b->plans) {
+        sgn_status st = require_ready(p);
+        if (st != SGN_OK) return st;
+        if (p->device != b->device) return fail(SGN_ERR_INVALID_ARGUMENT, "plan and batch are on different devices");
+    }
+    DeviceGuard g(b->device);
+    cudaError_t e;
+    // Order the batch after each plan's uploads and preparations.
+    std::vector<cudaStream_t> streams;
+    for (sgn_plan* p : b->plans)
+        if (p->stream != b->stream && std::find(streams.begin(), streams.end(), p->stream) == streams.end())
+            streams.push_back(p->stream);
+    while (b->plan_events.size() < streams.size()) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        b->plan_events.push_back(ev);
+    }
+    for (size_t i = 0; i < streams.size(); ++i) {
+        if ((e = cudaEventRecord(b->plan_events[i], streams[i])) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(b->stream, b->plan_events[i], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    }
+    // Plan table and work list: refreshed every run (poses, frame counts and options may change);
+    // items are (plan, surfel range) chunks ordered by decreasing cost (largest first).
+    b->h_plans.resize(b->plans.size());
+    for (size_t i = 0; i < b->plans.size(); ++i) b->h_plans[i] = make_params(b->plans[i]);
+    if (b->dirty) {
+        b->h_items.clear();
+        for (size_t i = 0; i < b->plans.size(); ++i) {
+            const sgn_plan* p = b->plans[i];
+            for (int f = 0; f < p->S; f += b->chunk)
+                b->h_items.push_back(WorkItem{int(i), f, std::min(b->chunk, p->S - f), 0});
+        }
+        std::stable_sort(b->h_items.begin(), b->h_items.end(), [&](const WorkItem& a, const WorkItem& c) {
+            const sgn_plan* pa = b->plans[a.plan];
+            const sgn_plan* pc = b->plans[c.plan];
+            const double ca = double(a.count) * pa->desc.patch * pa->desc.patch * std::max(1, pa->F);
+            const double cc = double(c.count) * pc->desc.patch * pc->desc.patch * std::max(1, pc->F);
+            return ca > cc;
+        });
+        b->n_items = int(b->h_items.size());
+        e = cudaMemcpyAsync(b->ws + off_items, b->h_items.data(), b->h_items.size() * sizeof(WorkItem),
+                            cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "work list upload");
+        b->dirty = false;
+    }
+    e = cudaMemcpyAsync(b->ws, b->h_plans.data(), b->h_plans.size() * sizeof(PlanParams), cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "plan table upload");
+    // The persistent launch (counter reset + kernel) is captured once per iteration count and
+    // replayed as a CUDA graph.
+    if (!b->exec || b->graph_iters != iters) {
+        batch_drop_graph(b);
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        const int per_sm = sgn::batch_blocks_per_sm(b->variant, 256);
+        if (per_sm <= 0) return fail(SGN_ERR_CUDA, "batch kernel cannot be resident");
+        b->graph_grid = sms * per_sm;
+        cudaStream_t cap = b->stream;
+        bool own = false;
+        if (cap == nullptr || cap == cudaStreamLegacy) {
+            if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "capture stream");
+            own = true;
+        }
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            if (own) cudaStreamDestroy(cap);
+            return cuda_fail(e, "cudaStreamBeginCapture");
+        }
+        int le = sgn::launch_gn_batch(reinterpret_cast<const PlanParams*>(b->ws), reinterpret_cast<const WorkItem*>(b->ws + off_items),
+                                      b->n_items, reinterpret_cast<int*>(b->ws + off_counter), iters, b->variant,
+                                      b->graph_grid, 256, cap);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cap, &graph);
+        if (own) cudaStreamDestroy(cap);
+        if (le) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(le, "batch kernel capture");
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        b->graph = graph;
+        if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) {
+            batch_drop_graph(b);
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        b->graph_iters = iters;
+    }
+    if ((e = cudaGraphLaunch(b->exec, b->stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    sgn::count_launch();
+    // Later work on each plan's stream (reads) waits for the batch.
+    if ((e = cudaEventRecord(b->done, b->stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (cudaStream_t s : streams)
+        if ((e = cudaStreamWaitEvent(s, b->done, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    for (sgn_plan* p : b->plans) p->depth_valid = true;
+    return SGN_OK;
+}
+
+sgn_status sgn_batch_sync(sgn_batch* b, uint64_t timeout_ns) {
+    if (!b) return fail(SGN_ERR_INVALID_ARGUMENT, "batch is NULL");
+    if (!b->ws) return fail(SGN_ERR_NOT_BOUND, "batch has no workspace");
+    DeviceGuard g(b->device);
+    return sync_event(b->done, b->stream, timeout_ns);
+}
+
+sgn_status sgn_batch_destroy(sgn_batch* b) {
+    if (!b) return SGN_OK;
+    DeviceGuard g(b->device);
+    batch_drop_graph(b);
+    if (b->done) cudaEventDestroy(b->done);
+    for (cudaEvent_t ev : b->plan_events) cudaEventDestroy(ev);
+    delete b;
+    return SGN_OK;
+}
+
+const char* sgn_last_error(void) { return g_last_error.c_str(); }
+uint64_t sgn_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+int sgn_abi_version(void) { return SGN_ABI_VERSION; }
+
+}  // extern "C"

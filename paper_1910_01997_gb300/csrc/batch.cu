@@ -1,0 +1,92 @@
+// Persistent batched Gauss-Newton: many keyframe problems (any size, patch, frame count and
+// texel dtype) in one launch.  Each warp pulls (plan, surfel range) work items from a device
+// work list through an atomic counter and runs the same per-surfel solver as the plain launch
+// (seeding, iterations, final cost, depth map).  The counter is reset by a memset on the same
+// stream before every launch; there is no waiting on other warps or blocks.
+#include <cuda_runtime.h>
+
+#include "gn_impl.cuh"
+
+namespace sgn {
+
+constexpr int kBatchBlock = 256;
+constexpr int kBatchWarps = kBatchBlock / 32;
+
+__host__ __device__ constexpr int batch_lanes(int variant, int P) {
+    return P == 16 ? 32 : (P == 8 ? (variant == 0 ? 16 : 32) : (variant == 0 ? 8 : 16));
+}
+
+int lanes_for_patch(int variant, int P) { return batch_lanes(variant, P); }
+
+template <int P, int G, int DT>
+__device__ __forceinline__ void run_chunk(const PlanParams* pp, int first, int count, int lane, int iters) {
+    constexpr int SPW = 32 / G;  // surfels per warp step
+    const int end = first + count;
+    for (int base = first; base < end; base += SPW) {
+        const int s = base + lane / G;
+        gn_surfel<P, G, DT>(pp, s < end ? s : pp->S, lane % G, iters, kModeSolve);
+    }
+}
+
+template <int V, int DT>
+__device__ __forceinline__ void dispatch_patch(const PlanParams* pp, const WorkItem& w, int lane, int iters) {
+    switch (pp->P) {
+        case 4: run_chunk<4, batch_lanes(V, 4), DT>(pp, w.first, w.count, lane, iters); break;
+        case 8: run_chunk<8, batch_lanes(V, 8), DT>(pp, w.first, w.count, lane, iters); break;
+        case 16: run_chunk<16, batch_lanes(V, 16), DT>(pp, w.first, w.count, lane, iters); break;
+        default: break;
+    }
+}
+
+template <int V>
+__global__ void __launch_bounds__(kBatchBlock) k_gn_batch(const PlanParams* __restrict__ plans,
+                                                          const WorkItem* __restrict__ items, int n_items,
+                                                          int* __restrict__ counter, int iters) {
+    __shared__ PlanParams spp[kBatchWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    PlanParams* my = &spp[warp];
+    int cur = -1;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const WorkItem w = items[it];
+        if (w.plan != cur) {
+            __syncwarp();
+            const int* src = reinterpret_cast<const int*>(plans + w.plan);
+            int* dst = reinterpret_cast<int*>(my);
+            for (int i = lane; i < int(sizeof(PlanParams) / 4); i += 32) dst[i] = __ldg(src + i);
+            __syncwarp();
+            cur = w.plan;
+        }
+        switch (my->dtype) {
+            case SGN_F32: dispatch_patch<V, SGN_F32>(my, w, lane, iters); break;
+            case SGN_F16: dispatch_patch<V, SGN_F16>(my, w, lane, iters); break;
+            case SGN_BF16: dispatch_patch<V, SGN_BF16>(my, w, lane, iters); break;
+            default: break;
+        }
+    }
+}
+
+int batch_blocks_per_sm(int variant, int block_threads) {
+    int n = 0;
+    cudaError_t e = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gn_batch<0>, block_threads, 0)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gn_batch<1>, block_threads, 0);
+    return e == cudaSuccess ? n : 0;
+}
+
+int launch_gn_batch(const PlanParams* d_plans, const WorkItem* d_items, int n_items, int* d_counter, int iters,
+                    int variant, int grid, int block_threads, void* stream) {
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (block_threads != kBatchBlock) return int(cudaErrorInvalidConfiguration);
+    cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return int(e);
+    if (variant == 0)
+        k_gn_batch<0><<<grid, block_threads, 0, st>>>(d_plans, d_items, n_items, d_counter, iters);
+    else
+        k_gn_batch<1><<<grid, block_threads, 0, st>>>(d_plans, d_items, n_items, d_counter, iters);
+    return int(cudaGetLastError());
+}
+
+}  // namespace sgn

@@ -1,0 +1,199 @@
+// Frame preparation, surfel initialisation/seeding and depth-map rendering kernels, and the
+// dtype dispatch of the Gauss-Newton launcher.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "sgn_internal.h"
+
+namespace sgn {
+
+int launch_gn_f32(const PlanParams& pp, int iters, int mode, int G, int block, void* stream);
+int launch_gn_f16(const PlanParams& pp, int iters, int mode, int G, int block, void* stream);
+int launch_gn_bf16(const PlanParams& pp, int iters, int mode, int G, int block, void* stream);
+
+int launch_gn(const PlanParams& pp, int iters, int mode, int lanes_per_surfel, int block_threads, void* stream) {
+    switch (pp.dtype) {
+        case SGN_F32: return launch_gn_f32(pp, iters, mode, lanes_per_surfel, block_threads, stream);
+        case SGN_F16: return launch_gn_f16(pp, iters, mode, lanes_per_surfel, block_threads, stream);
+        case SGN_BF16: return launch_gn_bf16(pp, iters, mode, lanes_per_surfel, block_threads, stream);
+        default: return int(cudaErrorInvalidValue);
+    }
+}
+
+// ------------------------------------------------------------------------------ frame preparation
+
+struct PrepArgs {
+    const float* src[kMaxFrames];
+    long long src_pitch[kMaxFrames];  // floats
+    void* dst;
+    long long plane;                  // texels per frame plane
+    int tex_pitch;                    // texels per row
+    int W, H, first, dtype;
+};
+
+// Intensity + central-difference gradient (the grad I of Eq. 8), packed as one texel per pixel:
+// (I, gx, gy, 0).  Border rows/columns get a zero gradient; the validity rule of the warp never
+// samples them.
+__global__ void __launch_bounds__(256) k_prep_frames(const __grid_constant__ PrepArgs a) {
+    const int f = blockIdx.z;
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= a.W || y >= a.H) return;
+    const long long sp = a.src_pitch[f];
+    const float* row = a.src[f] + (long long)y * sp;
+    const float I = __ldg(row + x);
+    const float gx = (x >= 1 && x <= a.W - 2) ? 0.5f * (__ldg(row + x + 1) - __ldg(row + x - 1)) : 0.0f;
+    const float gy = (y >= 1 && y <= a.H - 2) ? 0.5f * (__ldg(row + x + sp) - __ldg(row + x - sp)) : 0.0f;
+    const long long o = (long long)(a.first + f) * a.plane + (long long)y * a.tex_pitch + x;
+    if (a.dtype == SGN_F32) {
+        static_cast<float4*>(a.dst)[o] = make_float4(I, gx, gy, 0.0f);
+    } else if (a.dtype == SGN_F16) {
+        __half2 lo = __floats2half2_rn(I, gx), hi = __floats2half2_rn(gy, 0.0f);
+        uint2 v;
+        v.x = *reinterpret_cast<unsigned*>(&lo);
+        v.y = *reinterpret_cast<unsigned*>(&hi);
+        static_cast<uint2*>(a.dst)[o] = v;
+    } else {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(I, gx), hi = __floats2bfloat162_rn(gy, 0.0f);
+        uint2 v;
+        v.x = *reinterpret_cast<unsigned*>(&lo);
+        v.y = *reinterpret_cast<unsigned*>(&hi);
+        static_cast<uint2*>(a.dst)[o] = v;
+    }
+}
+
+int launch_prep_frames(const PlanParams& pp, const float* const* src, const size_t* src_pitch_floats, int first,
+                       int count, void* stream) {
+    if (count <= 0) return cudaSuccess;
+    PrepArgs a{};
+    for (int i = 0; i < count; ++i) {
+        a.src[i] = src[i];
+        a.src_pitch[i] = (long long)src_pitch_floats[i];
+    }
+    a.dst = const_cast<void*>(pp.tex);
+    a.plane = pp.tex_plane;
+    a.tex_pitch = pp.tex_pitch;
+    a.W = pp.W;
+    a.H = pp.H;
+    a.first = first;
+    a.dtype = pp.dtype;
+    dim3 block(32, 8), grid((pp.W + 31) / 32, (pp.H + 7) / 8, count);
+    k_prep_frames<<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return int(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------------------ surfel state
+
+// Initial working state from the initial surfels.  With seed != 0 every TO_SEED surfel is seeded
+// from its 8-connected VALID neighbours (Sec. 2.3): mean of Eq. 3 at its centre ray against each
+// neighbour's plane, normalised sum of the neighbours' camera-facing normals.
+__global__ void __launch_bounds__(256) k_init_state(const __grid_constant__ PlanParams pp, int seed) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= pp.S) return;
+    const int st0 = pp.state0[s];
+    float id = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
+    int status = SGN_SURFEL_EMPTY;
+    if (st0 == SGN_STATE_VALID) {
+        id = pp.id0[s];
+        nx = pp.n0[3 * s];
+        ny = pp.n0[3 * s + 1];
+        nz = pp.n0[3 * s + 2];
+        status = SGN_SURFEL_OK;
+    } else if (st0 == SGN_STATE_TO_SEED) {
+        status = SGN_SURFEL_UNSEEDED;
+        if (seed) {
+            const int TX = pp.TX, P = pp.P;
+            const int tx = s % TX, ty = s / TX;
+            const float half = 0.5f * float(P - 1);
+            const float rx = (float(tx * P) + half - pp.cx) * pp.ifx, ry = (float(ty * P) + half - pp.cy) * pp.ify;
+            float sid = 0.0f, snx = 0.0f, sny = 0.0f, snz = 0.0f;
+            int cid = 0, cn = 0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int qx = tx + dx, qy = ty + dy;
+                    if ((dx == 0 && dy == 0) || qx < 0 || qy < 0 || qx >= TX || qy >= pp.TY) continue;
+                    const int q = qy * TX + qx;
+                    if (pp.state0[q] != SGN_STATE_VALID) continue;
+                    const float rqx = (float(qx * P) + half - pp.cx) * pp.ifx;
+                    const float rqy = (float(qy * P) + half - pp.cy) * pp.ify;
+                    const float qnx = pp.n0[3 * q], qny = pp.n0[3 * q + 1], qnz = pp.n0[3 * q + 2];
+                    const float rqn = rqx * qnx + rqy * qny + qnz;
+                    const float v = pp.id0[q] * (rx * qnx + ry * qny + qnz) / rqn;
+                    if (isfinite(v) && v > 0.0f) {
+                        sid += v;
+                        ++cid;
+                    }
+                    const float sg = rqn < 0.0f ? 1.0f : -1.0f;
+                    snx += sg * qnx;
+                    sny += sg * qny;
+                    snz += sg * qnz;
+                    ++cn;
+                }
+            const float len = sqrtf(snx * snx + sny * sny + snz * snz);
+            if (cid > 0 && cn > 0 && len >= 1e-6f) {
+                id = sid / float(cid);
+                nx = snx / len;
+                ny = sny / len;
+                nz = snz / len;
+                status = SGN_SURFEL_OK | SGN_SURFEL_SEEDED;
+            }
+        }
+    }
+    pp.id[s] = id;
+    pp.n[3 * s] = nx;
+    pp.n[3 * s + 1] = ny;
+    pp.n[3 * s + 2] = nz;
+    pp.cost[s] = 0.0f;
+    pp.nres[s] = 0;
+    pp.status[s] = uint8_t(status);
+}
+
+int launch_seed(const PlanParams& pp, void* stream) {
+    const int block = 256, grid = (pp.S + block - 1) / block;
+    if (grid) k_init_state<<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(pp, 1);
+    return int(cudaGetLastError());
+}
+
+int launch_init_state(const PlanParams& pp, void* stream) {
+    const int block = 256, grid = (pp.S + block - 1) / block;
+    if (grid) k_init_state<<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(pp, 0);
+    return int(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------------------ depth map
+
+// Per-pixel inverse depth of Eq. 3 from the current surfels (tiles do not overlap, so each pixel
+// of a full tile belongs to its tile's surfel), and the generating surfel index (Sec. 2.2).
+__global__ void __launch_bounds__(256) k_render_depth(const __grid_constant__ PlanParams pp) {
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    const int P = pp.P;
+    if (x >= pp.TX * P || y >= pp.TY * P) return;
+    const int tx = x / P, ty = y / P, s = ty * pp.TX + tx;
+    const int st = pp.status[s] & 0x3f;
+    float v = 0.0f;
+    int idx = -1;
+    if (st != SGN_SURFEL_EMPTY && st != SGN_SURFEL_UNSEEDED) {
+        const float half = 0.5f * float(P - 1);
+        const float rsx = (float(tx * P) + half - pp.cx) * pp.ifx, rsy = (float(ty * P) + half - pp.cy) * pp.ify;
+        const float nx = pp.n[3 * s], ny = pp.n[3 * s + 1], nz = pp.n[3 * s + 2], ids = pp.id[s];
+        const float e = ((float(x - tx * P) - half) * pp.ifx * nx + (float(y - ty * P) - half) * pp.ify * ny) /
+                        (rsx * nx + rsy * ny + nz);
+        const float idu = fmaf(ids, e, ids);
+        if (idu > 0.0f && isfinite(idu)) {
+            v = idu;
+            idx = s;
+        }
+    }
+    pp.depth[(size_t)y * pp.W + x] = v;
+    pp.sidx[(size_t)y * pp.W + x] = idx;
+}
+
+int launch_render_depth(const PlanParams& pp, void* stream) {
+    dim3 block(32, 8), grid((pp.TX * pp.P + 31) / 32, (pp.TY * pp.P + 7) / 8);
+    if (grid.x && grid.y) k_render_depth<<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(pp);
+    return int(cudaGetLastError());
+}
+
+}  // namespace sgn

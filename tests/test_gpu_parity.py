@@ -1,0 +1,252 @@
+"""GPU (CUDA, through the C ABI) against the FP64 oracle, element by element on seeded inputs."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import angle_deg, compare, gpu_solve, oracle_solve
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL = json.load(open(os.path.join(HERE, "tolerances.json")))
+WELL = TOL["well_posed"]
+
+
+def _report(name, st):
+    keys = [k for k in st if k not in ("rel", "ang", "mask")]
+    print(name, {k: st[k] for k in keys})
+
+
+def _check(prob, g, o, dtype, name, min_frac=0.5):
+    st = compare(prob, g, o, margin_px=WELL["margin_px"], min_normal_eig=WELL["min_tangent_eig"])
+    _report(name, st)
+    tol = TOL["parity"][dtype]
+    assert st["n"] >= min_frac * st["n_usable"], st["excluded"]
+    assert st["depth_max"] <= tol["depth_rel"], (st["depth_max"], st["depth_p99"])
+    assert st["ang_max"] <= tol["normal_deg"], (st["ang_max"], st["ang_p99"])
+    # statuses agree except where a decision sits on a rounding edge
+    assert st["status_mismatch"] <= max(3, 0.01 * prob.S)
+    return st
+
+
+def test_tiny_parity_f32():
+    """160x120, three planes, 4x4 surfels, two frames, 10 iterations."""
+    prob = synth.tiny_problem(0)
+    g, o = gpu_solve(prob, 10), oracle_solve(prob, 10)
+    _check(prob, g, o, "f32", "tiny")
+
+
+def test_room_parity_f32_full_size():
+    """640x480 box room, 8x8 surfels (4800), 5 frames, 20 % seeded, noise 0.01, 10 iterations: the
+    benchmark workload in the benchmark's launch configuration, compared surfel by surfel."""
+    prob = synth.room_problem(0)
+    g, o = gpu_solve(prob, 10), oracle_solve(prob, 10)
+    st = _check(prob, g, o, "f32", "room")
+    seeded = (o["status"] & oracle.SEEDED_FLAG) != 0
+    assert np.array_equal(seeded, (g["status"] & 0x40) != 0)
+    # per-pixel inverse depth (Sec. 2.2) of compared surfels
+    m = st["mask"][np.maximum(g["sidx"], 0)] & (g["sidx"] >= 0)
+    rel = np.abs(g["inv_depth"][m] / o["inv_depth"][m] - 1)
+    assert rel.max() <= 2 * TOL["parity"]["f32"]["depth_rel"]
+    assert np.array_equal(g["sidx"] >= 0, o["sidx"] >= 0) or (np.mean((g["sidx"] >= 0) != (o["sidx"] >= 0)) < 1e-3)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_precision_split_1280x720(dtype):
+    """1280x720, 8 frames, 8x8 surfels (14400): texels in FP32/FP16/BF16, FP32 accumulation,
+    FP64 solves for ill-conditioned normal equations."""
+    prob = synth.room_problem(1, W=1280, H=720, F=8)
+    g, o = gpu_solve(prob, 10, dtype=dtype), oracle_solve(prob, 10)
+    _check(prob, g, o, dtype, f"precision {dtype}", min_frac=0.3)
+
+
+def test_seeding_parity():
+    """Sec. 2.3 seeding alone (zero iterations): seeded inverse depth and normal per surfel."""
+    prob = synth.room_problem(2, seed_frac=0.3)
+    g, o = gpu_solve(prob, 0), oracle_solve(prob, 0)
+    assert np.array_equal(g["status"], o["status"])
+    m = (o["status"] & oracle.SEEDED_FLAG) != 0
+    assert m.sum() > 1000
+    assert np.abs(g["id"][m] / o["id"][m] - 1).max() < 2e-6
+    assert angle_deg(g["n"][m], o["n"][m]).max() < 2e-3
+    v = prob.state == synth.VALID
+    assert np.array_equal(g["id"][v], prob.id0[v].astype(np.float32))
+
+
+def test_depth_map_from_given_surfels():
+    """Eq. 3 per pixel from the initial (unoptimised) surfels."""
+    prob = synth.room_problem(3, seed_frac=0.0)
+    g, o = gpu_solve(prob, 0), oracle_solve(prob, 0)
+    assert np.array_equal(g["sidx"], o["sidx"])
+    m = g["sidx"] >= 0
+    assert np.abs(g["inv_depth"][m] / o["inv_depth"][m] - 1).max() < 1e-5
+
+
+def test_mapping_variants_agree():
+    prob = synth.room_problem(4)
+    base = gpu_solve(prob, 10, lanes=16)
+    o = oracle_solve(prob, 10)
+    for lanes, block in ((8, 256), (32, 256), (16, 128), (32, 64)):
+        g = gpu_solve(prob, 10, lanes=lanes, block=block)
+        _check(prob, g, o, "f32", f"mapping {lanes}/{block}")
+        m = ((g["status"] & 0x3F) == 0) & ((base["status"] & 0x3F) == 0) & (o["margin"] > 1e-3)
+        assert np.median(np.abs(g["id"][m] / base["id"][m] - 1)) < 1e-6
+
+
+def test_run_after_seed_equals_solve():
+    prob = synth.room_problem(5)
+
+    def steps(plan):
+        plan.seed()
+        plan.run(4)
+        plan.run(6)
+
+    g = gpu_solve(prob, 0, steps=steps)
+    s = gpu_solve(prob, 10)
+    assert np.array_equal(g["status"] & 0x40, s["status"] & 0x40)
+    m = ((g["status"] & 0x3F) == 0) & ((s["status"] & 0x3F) == 0)
+    assert np.median(np.abs(g["id"][m] / s["id"][m] - 1)) < 1e-6
+
+
+def test_checkpoint_resume_is_bit_exact():
+    prob = synth.room_problem(6)
+
+    def five_five(plan):
+        plan.solve(5)
+        blob = plan.export_state()
+        plan.run(3)  # diverge, then restore
+        plan.import_state(blob)
+        plan.run(5)
+
+    a = gpu_solve(prob, 0, steps=five_five)
+    b = gpu_solve(prob, 0, steps=lambda plan: (plan.solve(5), plan.run(5)))
+    for k in ("id", "n", "cost", "nres", "status"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_device_inputs_equal_host_inputs():
+    import torch
+
+    import paper_1910_01997_gb300 as sgn
+
+    prob = synth.room_problem(7)
+    host = gpu_solve(prob, 6)
+    plan = sgn.Plan(prob.W, prob.H, prob.P, prob.F)
+    plan.set_intrinsics(*prob.cam)
+    plan.set_keyframe(torch.from_numpy(prob.keyframe).cuda())
+    plan.set_frames(torch.from_numpy(prob.frames).cuda(), prob.poses)
+    plan.init_surfels(torch.from_numpy(prob.id0.astype(np.float32)).cuda(),
+                      torch.from_numpy(prob.n0.astype(np.float32)).cuda(), torch.from_numpy(prob.state).cuda())
+    plan.solve(6)
+    dev = plan.read_surfels(device=True)
+    torch.cuda.synchronize()
+    for k in ("id", "n", "cost", "nres", "status"):
+        assert np.array_equal(dev[k].cpu().numpy(), host[k]), k
+
+
+def test_edge_cases():
+    prob = synth.tiny_problem(1)
+    # all empty
+    p2 = synth.Problem(**{**prob.__dict__, "state": np.zeros(prob.S, np.uint8)})
+    g = gpu_solve(p2, 3)
+    assert np.all(g["status"] == 1) and np.all(g["sidx"] == -1) and np.all(g["inv_depth"] == 0)
+    # all TO_SEED: nothing to seed from
+    p3 = synth.Problem(**{**prob.__dict__, "state": np.full(prob.S, 2, np.uint8)})
+    g = gpu_solve(p3, 3)
+    assert np.all(g["status"] == 2)
+    # min_residuals above the sample count: no update, UNDERDETERMINED
+    g = gpu_solve(prob, 3, min_residuals=33)
+    o = oracle_solve(prob, 3, min_residuals=33)
+    assert np.all((g["status"] & 0x3F) == 3) and np.array_equal(g["status"], o["status"])
+    assert np.array_equal(g["id"], prob.id0.astype(np.float32))
+    # zero iterations: initial parameters, cost at the initial parameters
+    g, o = gpu_solve(prob, 0), oracle_solve(prob, 0)
+    assert np.array_equal(g["id"], prob.id0.astype(np.float32))
+    m = (o["status"] & 0x3F) == 0
+    assert np.allclose(g["cost"][m], o["cost"][m], rtol=1e-3, atol=1e-7)
+    assert np.array_equal(g["nres"][o["margin"] > 1e-3], o["nres"][o["margin"] > 1e-3])
+
+
+def test_depth_only_ablation_keeps_normals():
+    prob = synth.room_problem(8)
+    g = gpu_solve(prob, 10, optimize_normal=False)
+    o = oracle_solve(prob, 10, optimize_normal=False)
+    v = prob.state == synth.VALID
+    assert np.array_equal(g["n"][v], prob.n0[v].astype(np.float32))
+    st = compare(prob, g, o, margin_px=WELL["margin_px"])
+    _report("depth-only", st)
+    assert st["depth_max"] <= TOL["parity"]["f32"]["depth_rel"]
+
+
+def test_ragged_and_degenerate_sizes():
+    for (W, H, P, F) in ((157, 113, 8, 3), (64, 40, 16, 2), (24, 16, 4, 1)):
+        sc = synth.room_scene(11, W, H, max(F, 1))
+        prob = synth.make_problem(sc, P, noise_sigma=0.01, seed_frac=0.2, seed=11)
+        g, o = gpu_solve(prob, 8), oracle_solve(prob, 8)
+        st = compare(prob, g, o, margin_px=WELL["margin_px"], min_normal_eig=WELL["min_tangent_eig"])
+        _report(f"ragged {W}x{H} P{P}", st)
+        if st["n"]:
+            assert st["depth_max"] <= TOL["parity"]["f32"]["depth_rel"]
+        # pixels outside full tiles keep the cleared map
+        assert np.all(g["sidx"][(H // P) * P:, :] == -1) and np.all(g["sidx"][:, (W // P) * P:] == -1)
+
+
+def test_max_frames():
+    sc = synth.room_scene(12, 320, 240, 16)
+    prob = synth.make_problem(sc, 8, noise_sigma=0.01, seed_frac=0.2, seed=12)
+    assert prob.F == 16
+    g, o = gpu_solve(prob, 6), oracle_solve(prob, 6)
+    _check(prob, g, o, "f32", "16 frames")
+
+
+def test_sync_deadline_reports_timeout_then_completes():
+    import paper_1910_01997_gb300 as sgn
+
+    prob = synth.room_problem(0)
+    plan = sgn.Plan(prob.W, prob.H, prob.P, prob.F)
+    plan.set_intrinsics(*prob.cam)
+    plan.set_keyframe(prob.keyframe)
+    plan.set_frames(prob.frames, prob.poses)
+    plan.init_surfels(prob.id0, prob.n0, prob.state)
+    plan.sync()
+    plan.solve(2000)
+    st = sgn._status("sgn_sync", plan.handle, 1)
+    assert st in (sgn.SGN_ERR_TIMEOUT, sgn.SGN_OK)
+    if st == sgn.SGN_ERR_TIMEOUT:
+        assert "deadline" in sgn.sgn_last_error()
+    plan.sync()
+    out = plan.read_surfels()
+    assert np.isfinite(out["id"]).all()
+
+
+def test_workspace_checks():
+    import torch
+
+    import paper_1910_01997_gb300 as sgn
+
+    h = sgn.sgn_plan_create(sgn.sgn_plan_desc_default(64, 64, 8, 2))
+    need = sgn.sgn_plan_workspace_bytes(h)
+    ws = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    with pytest.raises(sgn.SgnError) as e:
+        sgn.sgn_plan_bind(h, ws.data_ptr(), need - 1, 0)
+    assert e.value.status == sgn.SGN_ERR_WORKSPACE_TOO_SMALL
+    with pytest.raises(sgn.SgnError) as e:
+        sgn.sgn_plan_bind(h, ws.data_ptr() + 16, need, 0)
+    assert e.value.status == sgn.SGN_ERR_INVALID_ARGUMENT
+    host = np.zeros(need, np.uint8)
+    with pytest.raises(sgn.SgnError):
+        sgn.sgn_plan_bind(h, host.ctypes.data, need, 0)
+    sgn.sgn_plan_bind(h, ws.data_ptr(), need, 0)
+    with pytest.raises(sgn.SgnError) as e:
+        sgn.sgn_run(h, 1)
+    assert e.value.status == sgn.SGN_ERR_STATE
+    bad_pose = np.eye(3, 4) * 2
+    img = np.zeros((64, 64), np.float32)
+    with pytest.raises(sgn.SgnError) as e:
+        sgn.sgn_set_frame(h, 0, img.ctypes.data, 256, sgn.SGN_HOST, np.ascontiguousarray(bad_pose).ctypes.data)
+    assert e.value.status == sgn.SGN_ERR_INVALID_ARGUMENT
+    sgn.sgn_plan_destroy(h)
