@@ -1,0 +1,338 @@
+"""Benchmark: surfel-pixel Gauss-Newton residuals per second on one 640x480 keyframe solve.
+
+Workload (one step = the whole hot path on one keyframe): a seeded 640x480 box-room scene, one
+keyframe and 5 observing frames, 8x8 surfels (4800), 20 % of them seeded from neighbours, noise
+sigma 0.01, 10 Gauss-Newton iterations.  A step prepares the frames (intensity + gradient texels),
+seeds, iterates, evaluates the final cost and renders the inverse-depth map, then copies the surfels
+and the map out.  Inputs are resident in device memory when the timed region starts; the L2 cache
+is flushed (a 512 MB write) before every timed step.  "e2e" repeats the step through the C ABI from
+page-locked host buffers, host<->device copies included.
+
+Multi-GPU: keyframes are independent, so N ranks run N independent replicas (weak scaling, no
+collective on the data path); the time is the maximum over ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="room640x480_f5_p8_seed20_it10", width=640, height=480, frames=5, patch=8,
+                surfels=4800, seed_fraction=0.2, noise_sigma=0.01, iterations=10, texels="f32")
+BYTES_PER_RESIDUAL = {"f32": 12, "f16": 6, "bf16": 6}
+KERNEL_SOURCES = ["paper_1910_01997_gb300/csrc/gn_impl.cuh", "paper_1910_01997_gb300/csrc/gn_kernels.cuh",
+                  "paper_1910_01997_gb300/csrc/gn_f32.cu"]
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def make_problem(rank: int):
+    import synth
+
+    return synth.room_problem(seed=rank, W=WORKLOAD["width"], H=WORKLOAD["height"], F=WORKLOAD["frames"],
+                              P=WORKLOAD["patch"], noise_sigma=WORKLOAD["noise_sigma"],
+                              seed_frac=WORKLOAD["seed_fraction"])
+
+
+def residuals_per_step(prob) -> int:
+    return prob.S * prob.P * prob.P * prob.F * WORKLOAD["iterations"]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the Gauss-Newton kernel from the committed ncu summary, when it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "gn_room640_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    return d.get("dram_bytes_per_launch") if d.get("kernel_sha") == kernel_sha() else None
+
+
+def cpu_baseline(prob, budget_s: float = 10.0):
+    """The FP64 oracle (as it stands) on the host cores: whole keyframe solves for ~budget_s."""
+    import oracle
+
+    ob = oracle.Problem.from_synth(prob)
+    prm = oracle.params()
+    n, t0, threads = 0, time.perf_counter(), 0
+    while True:
+        out = ob.solve(prm, WORKLOAD["iterations"], prob.id0, prob.n0, prob.state, depth_map=True)
+        threads = out["threads"]
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    return {"value": n * residuals_per_step(prob) / dt, "unit": "residuals/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} whole keyframe solves of the benchmark workload ({dt:.1f} s, FP64 C, OpenMP over surfels)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1910_01997_gb300 as sgn
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    prob = make_problem(rank)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    W, H, F, S = prob.W, prob.H, prob.F, prob.S
+    iters = WORKLOAD["iterations"]
+    with torch.cuda.stream(stream):
+        plan = sgn.Plan(W, H, prob.P, F, WORKLOAD["texels"], stream=stream)
+        plan.set_intrinsics(*prob.cam)
+        # inputs resident in HBM
+        d_kf = torch.from_numpy(prob.keyframe).to(dev)
+        d_frames = torch.from_numpy(prob.frames).to(dev)
+        d_id0 = torch.from_numpy(prob.id0.astype(np.float32)).to(dev)
+        d_n0 = torch.from_numpy(prob.n0.astype(np.float32)).to(dev)
+        d_state = torch.from_numpy(prob.state).to(dev)
+        out = dict(id=torch.empty(S, device=dev), n=torch.empty(S, 3, device=dev), cost=torch.empty(S, device=dev),
+                   nres=torch.empty(S, dtype=torch.int32, device=dev), status=torch.empty(S, dtype=torch.uint8, device=dev),
+                   depth=torch.empty(H, W, device=dev), sidx=torch.empty(H, W, dtype=torch.int32, device=dev))
+        flush = torch.empty(max(1, args.flush_mb) << 20, dtype=torch.uint8, device=dev)
+        frame_ptrs = [d_frames[i] for i in range(F)]
+        pose = prob.poses
+
+        def step(k0=None, k1=None):
+            plan.set_keyframe(d_kf)
+            plan.set_frames(frame_ptrs, pose)
+            plan.init_surfels(d_id0, d_n0, d_state)
+            if k0 is not None:
+                k0.record(stream)
+            plan.solve(iters)
+            if k1 is not None:
+                k1.record(stream)
+            sgn.sgn_read_surfels(plan.handle, out["id"].data_ptr(), out["n"].data_ptr(), out["cost"].data_ptr(),
+                                 out["nres"].data_ptr(), out["status"].data_ptr(), sgn.SGN_DEVICE)
+            sgn.sgn_read_depth_map(plan.handle, out["depth"].data_ptr(), out["sidx"].data_ptr(), sgn.SGN_DEVICE)
+
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        stream.synchronize()
+        plan._keep.clear()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        launches0 = sgn.sgn_launch_count()
+        with ClockSampler(local) as clocks:
+            time.sleep(0.3)
+            for i in range(args.steps):
+                flush.zero_()
+                s0, s1, k0, k1 = ev[i]
+                s0.record(stream)
+                step(k0, k1)
+                s1.record(stream)
+                if i % 32 == 31:
+                    plan._keep.clear()
+            stream.synchronize()
+            # keep sampling for a moment under the same load for a steadier clock reading
+        launches = sgn.sgn_launch_count() - launches0
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        step_ms = [e[0].elapsed_time(e[1]) for e in ev]
+        kern_ms = [e[2].elapsed_time(e[3]) for e in ev]
+        total_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+
+        # end to end through the C ABI from page-locked host buffers
+        h_kf = torch.from_numpy(prob.keyframe).pin_memory()
+        h_frames = torch.from_numpy(prob.frames).pin_memory()
+        h_id0 = torch.from_numpy(prob.id0.astype(np.float32)).pin_memory()
+        h_n0 = torch.from_numpy(prob.n0.astype(np.float32)).pin_memory()
+        h_state = torch.from_numpy(prob.state).pin_memory()
+        h_out = dict(id=torch.empty(S).pin_memory(), n=torch.empty(S, 3).pin_memory(), cost=torch.empty(S).pin_memory(),
+                     nres=torch.empty(S, dtype=torch.int32).pin_memory(), status=torch.empty(S, dtype=torch.uint8).pin_memory(),
+                     depth=torch.empty(H, W).pin_memory(), sidx=torch.empty(H, W, dtype=torch.int32).pin_memory())
+        h_frame_list = [h_frames[i] for i in range(F)]
+
+        def e2e_step():
+            plan.set_keyframe(h_kf)
+            plan.set_frames(h_frame_list, pose)
+            plan.init_surfels(h_id0, h_n0, h_state)
+            plan.solve(iters)
+            sgn.sgn_read_surfels(plan.handle, h_out["id"].data_ptr(), h_out["n"].data_ptr(), h_out["cost"].data_ptr(),
+                                 h_out["nres"].data_ptr(), h_out["status"].data_ptr(), sgn.SGN_HOST)
+            sgn.sgn_read_depth_map(plan.handle, h_out["depth"].data_ptr(), h_out["sidx"].data_ptr(), sgn.SGN_HOST)
+            plan.sync()
+
+        for _ in range(max(1, args.warmup)):
+            flush.zero_()
+            e2e_step()
+        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            e2e_ev[i][0].record(stream)
+            e2e_step()
+            e2e_ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+    h2d = prob.keyframe.nbytes + prob.frames.nbytes + S * (4 + 12 + 1)
+    d2h = S * (4 + 12 + 4 + 4 + 1) + W * H * 8
+
+    res = residuals_per_step(prob)
+    value = world * res * args.steps / (total_ms / 1e3)
+    peak, peak_kind = measured_peaks()
+    kern_avg_s = statistics.mean(kern_ms) / 1e3
+    achieved = res * BYTES_PER_RESIDUAL[WORKLOAD["texels"]] / kern_avg_s / 1e9
+    clk = clocks.summary()
+    line = {
+        "metric": "surfel-pixel GN residuals/s (640x480 keyframe solve)",
+        "value": value, "unit": "residuals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded box-room renders, sigma 0.01 noise)",
+        "config": {**WORKLOAD, "l2": (f"flushed ({args.flush_mb} MB write) before every timed step" if args.flush_mb >= 256
+                                      else f"NOT flushed ({args.flush_mb} MB write): profiling run only"),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic(), "kernel": "k_gn<8,16,f32>",
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "note": "algorithmic bytes = residuals x 12 B (I, gx, gy in FP32) per launch / CUDA-event launch time"},
+        "e2e": {"value": world * res * args.steps / (e2e_ms / 1e3), "unit": "residuals/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "kernel_ms_per_step": statistics.mean(kern_ms),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    prob = make_problem(0)
+    ob = oracle.Problem.from_synth(prob)
+    prm = oracle.params()
+    res = residuals_per_step(prob)
+    threads = 0
+    for _ in range(args.warmup):
+        threads = ob.solve(prm, WORKLOAD["iterations"], prob.id0, prob.n0, prob.state)["threads"]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ob.solve(prm, WORKLOAD["iterations"], prob.id0, prob.n0, prob.state)
+    dt = time.perf_counter() - t0
+    value = res * args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": "surfel-pixel GN residuals/s (640x480 keyframe solve)", "value": value,
+        "unit": "residuals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded box-room renders, sigma 0.01 noise)", "config": WORKLOAD,
+        "cpu_baseline": {"value": value, "unit": "residuals/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} whole keyframe solves of the benchmark workload"},
+        "e2e": {"value": value, "unit": "residuals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written before each timed step")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

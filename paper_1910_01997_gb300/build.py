@@ -50,7 +50,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+              *os.environ.get("SGN_NVCC_FLAGS", "").split()]
     jobs = []
     for src in _sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

@@ -188,6 +188,10 @@ PlanParams make_params(const sgn_plan* p) {
     pp.fy = float(p->fy);
     pp.cx = float(p->cx);
     pp.cy = float(p->cy);
+    pp.fx_lo = float(p->fx - double(pp.fx));
+    pp.fy_lo = float(p->fy - double(pp.fy));
+    pp.cx_lo = float(p->cx - double(pp.cx));
+    pp.cy_lo = float(p->cy - double(pp.cy));
     pp.ifx = float(1.0 / p->fx);
     pp.ify = float(1.0 / p->fy);
     pp.huber_k = d.huber_k;
@@ -212,27 +216,16 @@ PlanParams make_params(const sgn_plan* p) {
     pp.status = reinterpret_cast<uint8_t*>(b + L.status);
     pp.depth = reinterpret_cast<float*>(b + L.depth);
     pp.sidx = reinterpret_cast<int32_t*>(b + L.sidx);
-    // Eq. 6 in homogeneous pixel coordinates: M = K R K^-1, b = K t (computed in double).
-    const double K[9] = {p->fx, 0, p->cx, 0, p->fy, p->cy, 0, 0, 1};
-    const double Ki[9] = {1.0 / p->fx, 0, -p->cx / p->fx, 0, 1.0 / p->fy, -p->cy / p->fy, 0, 0, 1};
     for (int f = 0; f < p->F; ++f) {
-        const double* T = p->T[f];
-        double KR[9];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) {
-                double v = 0.0;
-                for (int k = 0; k < 3; ++k) v += K[3 * i + k] * T[4 * k + j];
-                KR[3 * i + j] = v;
-            }
         for (int i = 0; i < 3; ++i) {
             for (int j = 0; j < 3; ++j) {
-                double v = 0.0;
-                for (int k = 0; k < 3; ++k) v += KR[3 * i + k] * Ki[3 * k + j];
-                pp.frames[f].M[3 * i + j] = float(v);
+                const double v = p->T[f][4 * i + j];
+                pp.frames[f].R[3 * i + j] = float(v);
+                pp.frames[f].R_lo[3 * i + j] = float(v - double(float(v)));
             }
-            double v = 0.0;
-            for (int k = 0; k < 3; ++k) v += K[3 * i + k] * T[4 * k + 3];
-            pp.frames[f].b[i] = float(v);
+            const double v = p->T[f][4 * i + 3];
+            pp.frames[f].t[i] = float(v);
+            pp.frames[f].t_lo[i] = float(v - double(float(v)));
         }
     }
     return pp;

