@@ -80,7 +80,8 @@ def _load():
                                            ctypes.POINTER(c_i), _D, _D, _D]),
                 "orc_damped_step": (c_i, [_D, _D, c_d, c_i, _D]),
                 "orc_apply_step": (None, [_D, c_d, _D, _D, _D]),
-                "orc_gauss_newton": (c_i, [_V, ctypes.POINTER(Params), c_i, c_i, _D, _D, _V, _D, _V, _V, _V]),
+                "orc_gauss_newton": (c_i, [_V, ctypes.POINTER(Params), c_i, c_i, _D, _D, _V, _D, _V, _V, _V, _V, _V]),
+                "orc_problem_create_planes": (_V, [c_i, c_i, c_i, c_d, c_d, c_d, c_d, _V, c_i, _D, _D, _D, _D]),
                 "orc_seed": (None, [_V, _D, _D, _V, _D, _D, _V]),
                 "orc_depth_map": (None, [_V, _D, _D, _V, _D, _V]),
                 "orc_cost_grid": (None, [_V, ctypes.POINTER(Params), c_i, ctypes.c_long, _D, _D, _D, _V]),
@@ -219,6 +220,22 @@ class Problem:
     def from_synth(cls, prob):
         return cls(prob.W, prob.H, prob.P, prob.cam, prob.keyframe, prob.frames, prob.poses)
 
+    @classmethod
+    def from_planes(cls, W, H, P, cam, keyframe, I, gx, gy, poses):
+        """Problem whose frame intensity and gradient planes (F, H, W) are given, not computed."""
+        self = cls.__new__(cls)
+        lib = _load()
+        self.W, self.H, self.P = int(W), int(H), int(P)
+        self.cam = tuple(float(c) for c in cam)
+        kf = np.ascontiguousarray(keyframe, dtype=np.float32)
+        I, gx, gy = (np.ascontiguousarray(a, dtype=np.float64) for a in (I, gx, gy))
+        ps = np.ascontiguousarray(poses, dtype=np.float64)
+        self.F = I.shape[0]
+        self.S = (self.W // self.P) * (self.H // self.P)
+        self._h = lib.orc_problem_create_planes(self.W, self.H, self.P, *self.cam, _v(kf), self.F, _d(I), _d(gx),
+                                                _d(gy), _d(ps))
+        return self
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h and _lib is not None:
@@ -257,12 +274,17 @@ class Problem:
         cost, nres = np.empty(self.S), np.empty(self.S, np.int32)
         margin = np.empty(self.S) if diagnostics else None
         H_last = np.empty(6 * self.S) if diagnostics else None
+        path_n = np.empty(self.S) if diagnostics else None
+        path_id = np.empty(self.S) if diagnostics else None
         used = _load().orc_gauss_newton(self._h, ctypes.byref(prm), int(iters), int(nthreads), _d(id_s), _d(n),
-                                        _v(status), _d(cost), _v(nres), _v(margin), _v(H_last))
+                                        _v(status), _d(cost), _v(nres), _v(margin), _v(H_last), _v(path_n),
+                                        _v(path_id))
         out = dict(id=id_s, n=n.reshape(-1, 3), status=status, cost=cost, nres=nres, threads=used)
         if diagnostics:
             out["margin"] = margin
             out["H_last"] = H_last.reshape(-1, 6)
+            out["path_n"] = path_n
+            out["path_id"] = path_id
         return out
 
     def depth_map(self, id_s, n, status):

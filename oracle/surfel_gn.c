@@ -213,6 +213,27 @@ void* orc_problem_create(int W, int H, int P, double fx, double fy, double cx, d
     return pb;
 }
 
+/* Same as orc_problem_create, with the frame intensity and gradient planes given (F*H*W doubles
+ * each) instead of computed: the method run on images as some storage format holds them. */
+void* orc_problem_create_planes(int W, int H, int P, double fx, double fy, double cx, double cy, const float* keyframe,
+                                int F, const double* I, const double* gx, const double* gy, const double* poses) {
+    orc_problem* pb = (orc_problem*)calloc(1, sizeof(orc_problem));
+    long n = (long)W * H;
+    pb->W = W; pb->H = H; pb->P = P; pb->F = F;
+    pb->fx = fx; pb->fy = fy; pb->cx = cx; pb->cy = cy;
+    pb->kf = (double*)malloc(sizeof(double) * n);
+    pb->I = (double*)malloc(sizeof(double) * n * (F > 0 ? F : 1));
+    pb->gx = (double*)malloc(sizeof(double) * n * (F > 0 ? F : 1));
+    pb->gy = (double*)malloc(sizeof(double) * n * (F > 0 ? F : 1));
+    pb->T = (double*)malloc(sizeof(double) * 12 * (F > 0 ? F : 1));
+    for (long i = 0; i < n; ++i) pb->kf[i] = keyframe[i];
+    memcpy(pb->I, I, sizeof(double) * n * F);
+    memcpy(pb->gx, gx, sizeof(double) * n * F);
+    memcpy(pb->gy, gy, sizeof(double) * n * F);
+    memcpy(pb->T, poses, sizeof(double) * 12 * F);
+    return pb;
+}
+
 void orc_problem_destroy(void* p) {
     orc_problem* pb = (orc_problem*)p;
     if (!pb) return;
@@ -340,11 +361,14 @@ void orc_apply_step(const double n[3], double id_s, const double delta[3], doubl
  * After the iterations, one more evaluation at the returned parameters gives cost (the
  * "last residual" kept with each surfel, Sec. 2.1) and nres.  Optional per-surfel
  * diagnostics: margin (smallest distance of any sample used to the validity bounds,
- * over all evaluations) and H_last (6 per surfel, undamped H of the last iteration).
+ * over all evaluations), H_last (6 per surfel, undamped H of the last iteration), path_n (sum of
+ * the normal's rotation over the accepted steps, degrees) and path_id (sum of |relative inverse
+ * depth change| over the accepted steps).
  * Returns the number of threads used.
  */
 int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthreads, double* id, double* n,
-                     uint8_t* status, double* cost, int32_t* nres, double* margin, double* H_last) {
+                     uint8_t* status, double* cost, int32_t* nres, double* margin, double* H_last, double* path_n,
+                     double* path_id) {
     const orc_problem* pb = (const orc_problem*)p;
     int S = (pb->W / pb->P) * (pb->H / pb->P);
     int used = 1;
@@ -364,6 +388,8 @@ int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthrea
                 cost[s] = 0.0;
                 nres[s] = 0;
                 if (margin) margin[s] = mg;
+                if (path_n) path_n[s] = 0.0;
+                if (path_id) path_id[s] = 0.0;
                 continue;
             }
             double ids = id[s], ns[3] = {n[3 * s], n[3 * s + 1], n[3 * s + 2]};
@@ -371,6 +397,7 @@ int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthrea
             double H[6], g[3], E, m;
             int cnt;
             if (H_last) for (int i = 0; i < 6; ++i) H_last[6 * s + i] = 0.0;
+            double pn = 0.0, pid = 0.0;
             for (int it = 0; it < iters; ++it) {
                 orc_eval_surfel(pb, prm, s, ids, ns, H, g, &E, &cnt, &m, NULL, NULL);
                 if (m < mg) mg = m;
@@ -403,6 +430,8 @@ int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthrea
                 if (dot3(n_new, r_s) > 0.0) {
                     n_new[0] = -n_new[0]; n_new[1] = -n_new[1]; n_new[2] = -n_new[2];
                 }
+                pn += acos(fmin(1.0, fabs(dot3(n_new, ns)))) * (180.0 / 3.14159265358979323846);
+                pid += fabs(id_new / ids - 1.0);
                 ids = id_new;
                 ns[0] = n_new[0]; ns[1] = n_new[1]; ns[2] = n_new[2];
                 outcome = OUT_OK;
@@ -415,6 +444,8 @@ int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthrea
             cost[s] = E;
             nres[s] = cnt;
             if (margin) margin[s] = mg;
+            if (path_n) path_n[s] = pn;
+            if (path_id) path_id[s] = pid;
         }
 #ifdef _OPENMP
     }

@@ -69,29 +69,60 @@ def ulp(x, dtype):
     return np.exp2(e - MANTISSA_BITS[dtype])
 
 
-def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=3e-5, seeds=(1, 2, 3), **opts):
+def stored_planes(frames, dtype):
+    """Intensity and central-difference gradient planes as a texel type stores them: intensities
+    rounded to the type, gradients as half differences of the rounded intensities (exact in FP32)
+    rounded to the type, zero on the border rows/columns.  Computed here in numpy from the inputs."""
+    Iq = quantize(frames, dtype).astype(np.float32)
+    gx = np.zeros_like(Iq)
+    gy = np.zeros_like(Iq)
+    gx[:, :, 1:-1] = np.float32(0.5) * (Iq[:, :, 2:] - Iq[:, :, :-2])
+    gy[:, 1:-1, :] = np.float32(0.5) * (Iq[:, 2:, :] - Iq[:, :-2, :])
+    return tuple(quantize(a, dtype).astype(np.float64) for a in (Iq, gx, gy))
+
+
+def oracle_solve_planes(prob, planes, iters, **opts):
+    ob = oracle.Problem.from_planes(prob.W, prob.H, prob.P, prob.cam, prob.keyframe, *planes, prob.poses)
+    out = ob.solve(oracle_params(**opts), iters, prob.id0, prob.n0, prob.state)
+    out["problem"] = ob
+    return out
+
+
+def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=3e-5, seeds=(1, 2, 3), planes=None,
+                  **opts):
     """Surfels whose oracle result after `iters` iterations is a stable function of the inputs.
 
     The oracle alone is re-run with the initial parameters perturbed by a relative eps and the frame
-    intensities perturbed at the rounding scale of the texel dtype (uniform +-ulp/2 per pixel for
-    each seed; for f32 +-2 ulp, standing for the FP32 arithmetic of a sample), plus, for FP16/BF16,
-    once with the frames rounded to that dtype.  A surfel is stable when every re-run keeps its
-    status and stays within half the tolerance of the unperturbed result: element-by-element parity
-    is only defined there.
+    data perturbed at the rounding scale of the texel type (uniform +-ulp/2 per pixel for each seed;
+    for FP32 +-2 ulp, standing for the FP32 arithmetic of a sample), plus, for FP16/BF16, once on
+    the intensity and gradient planes as that type stores them.  With `planes` (intensity and gradient planes given to the
+    oracle) those planes are perturbed by +-2 FP32 ulp.  A surfel is stable when every re-run keeps
+    its status and stays within half the tolerance of the unperturbed result, and when the path its
+    parameters travel over the iterations, times the condition number of its scaled normal
+    equations and 1e-6 (the relative FP32 error of one step), stays below half the tolerance:
+    element-by-element parity is only defined there.
     """
     prm = oracle_params(**opts)
-    runs = []
-    scale = 2.0 if dtype == "f32" else 0.5
+    stable = np.ones(prob.S, bool)
+    kappa = scaled_cond(base["H_last"]) if prm.optimize_normal else np.ones(prob.S)
+    with np.errstate(invalid="ignore"):
+        stable &= (base["path_n"] * kappa * 1e-6 <= 0.5 * tol_deg) & (base["path_id"] * kappa * 1e-6 <= 0.5 * tol_depth)
+    problems = []
     for k in seeds:
         rng = np.random.default_rng([k, 77])
-        frames = prob.frames + scale * ulp(prob.frames, dtype) * rng.uniform(-1, 1, prob.frames.shape)
-        runs.append((k, frames.astype(np.float32) if dtype != "f32" else frames))
-    if dtype != "f32":
-        runs.append((99, quantize(prob.frames, dtype)))
-    stable = np.ones(prob.S, bool)
-    for k, frames in runs:
+        if planes is not None:
+            pl = [a + 2.0 * ulp(a, "f32") * rng.uniform(-1, 1, a.shape) for a in planes]
+            problems.append((k, oracle.Problem.from_planes(prob.W, prob.H, prob.P, prob.cam, prob.keyframe, *pl,
+                                                           prob.poses)))
+        else:
+            scale = 2.0 if dtype == "f32" else 0.5
+            frames = prob.frames + scale * ulp(prob.frames, dtype) * rng.uniform(-1, 1, prob.frames.shape)
+            problems.append((k, oracle.Problem(prob.W, prob.H, prob.P, prob.cam, prob.keyframe, frames, prob.poses)))
+    if planes is None and dtype != "f32":
+        problems.append((99, oracle.Problem.from_planes(prob.W, prob.H, prob.P, prob.cam, prob.keyframe,
+                                                        *stored_planes(prob.frames, dtype), prob.poses)))
+    for k, ob in problems:
         rng = np.random.default_rng([k, 78])
-        ob = oracle.Problem(prob.W, prob.H, prob.P, prob.cam, prob.keyframe, frames, prob.poses)
         id1 = prob.id0 * (1.0 + eps * rng.standard_normal(prob.S))
         n1 = prob.n0 + eps * rng.standard_normal(prob.n0.shape)
         n1 /= np.maximum(np.linalg.norm(n1, axis=1, keepdims=True), 1e-30)
@@ -100,6 +131,20 @@ def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=3e-5, 
         stable &= np.abs(p["id"] / np.where(base["id"] != 0, base["id"], 1.0) - 1.0) <= 0.5 * tol_depth
         stable &= angle_deg(p["n"], base["n"]) <= 0.5 * tol_deg
     return stable
+
+
+def scaled_cond(H6):
+    """2-norm condition numbers of the Jacobi-scaled (unit-diagonal) 3x3 normal matrices."""
+    H = np.stack([np.asarray(H6)[:, i] for i in (0, 1, 2, 1, 3, 4, 2, 4, 5)], 1).reshape(-1, 3, 3)
+    d = np.einsum("nii->ni", H)
+    good = (d > 0).all(1)
+    out = np.full(len(H), np.inf)
+    if good.any():
+        sq = np.sqrt(d[good])
+        S = H[good] / (sq[:, :, None] * sq[:, None, :])
+        w = np.linalg.eigvalsh(S)
+        out[good] = w[:, -1] / np.maximum(w[:, 0], 1e-300)
+    return out
 
 
 def angle_deg(a, b):
