@@ -172,6 +172,35 @@ sgn_status sgn_state_bytes(const sgn_plan* plan, size_t* bytes);
 sgn_status sgn_export_state(sgn_plan* plan, void* host, size_t bytes);
 sgn_status sgn_import_state(sgn_plan* plan, const void* host, size_t bytes);
 
+/* ---- one solve that allocates nothing --------------------------------------------------- */
+
+/* The paper has no counterpart to this call; it serves callers that must not allocate device
+ * memory where they solve: code running while a stream is captured into a CUDA graph, real-time
+ * loops that may not take the allocator's locks or fail with out-of-memory mid-run, and host
+ * frameworks that hand out only the buffers they own.
+ *
+ * sgn_solve_static runs the same work as sgn_set_frames + sgn_init_surfels + sgn_solve + the reads,
+ * enqueued on cuda_stream, without a plan or workspace: every input and output is a caller-owned
+ * DEVICE pointer (all required; keyframe W x H floats with keyframe_pitch_bytes rows; frames[] is a
+ * host array of num_frames device pointers with frame_pitch_bytes rows; surfel arrays as in
+ * sgn_init_surfels / sgn_read_surfels; depth_map and surfel_index W x H, tightly packed) except
+ * desc, intrinsics (fx, fy, cx, cy) and poses (12 doubles per frame), which are host memory read
+ * during the call.  The packed frame texels go to a fixed device array of SGN_STATIC_SCRATCH_BYTES
+ * that the library owns: num_frames * height * round_up(width, 32) * (16 for FP32, 8 for FP16/BF16
+ * texels) must fit, else SGN_ERR_WORKSPACE_TOO_SMALL.  Every GPU that loads the library holds that
+ * array until the process exits.  All calls share it and it keeps the last call's contents; calls in
+ * sequence are independent (each rewrites what it reads), but calls whose work overlaps on the GPU
+ * race on it.  The first call on a device looks the array's address up (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  No cudaMalloc, cudaFree or
+ * other allocating routine is called. */
+#define SGN_STATIC_SCRATCH_BYTES (32u << 20)
+sgn_status sgn_solve_static(const sgn_plan_desc* desc, const double intrinsics[4], const float* keyframe,
+                            size_t keyframe_pitch_bytes, int num_frames, const float* const* frames,
+                            size_t frame_pitch_bytes, const double* poses, const float* inv_depth0,
+                            const float* normal0, const uint8_t* state0, int iters, float* inv_depth, float* normal,
+                            float* cost, int32_t* nres, uint8_t* status, float* depth_map, int32_t* surfel_index,
+                            void* cuda_stream);
+
 /* ---- batches: many keyframe plans in one persistent launch --------------------------- */
 
 /* A batch groups up to max_plans bound plans (any sizes, patches, frame counts, dtypes).

@@ -75,6 +75,8 @@ _SIGS = {
     "sgn_state_bytes": [_P, ctypes.POINTER(_SZ)],
     "sgn_export_state": [_P, _P, _SZ],
     "sgn_import_state": [_P, _P, _SZ],
+    "sgn_solve_static": [ctypes.POINTER(sgn_plan_desc), _P, _P, _SZ, _I, _P, _SZ, _P, _P, _P, _P, _I,
+                         _P, _P, _P, _P, _P, _P, _P, _P],
     "sgn_batch_create": [_I, ctypes.POINTER(_P)],
     "sgn_batch_add": [_P, _P],
     "sgn_batch_clear": [_P],
@@ -207,6 +209,19 @@ def sgn_export_state(plan, host_ptr, nbytes):
 
 def sgn_import_state(plan, host_ptr, nbytes):
     _call("sgn_import_state", plan, host_ptr, nbytes)
+
+
+SGN_STATIC_SCRATCH_BYTES = 32 << 20
+
+
+def sgn_solve_static(desc, intrinsics_ptr, keyframe_ptr, keyframe_pitch_bytes, num_frames, frame_ptrs_ptr,
+                     frame_pitch_bytes, poses_ptr, inv_depth0_ptr, normal0_ptr, state0_ptr, iters, inv_depth_ptr,
+                     normal_ptr, cost_ptr, nres_ptr, status_ptr, depth_map_ptr, surfel_index_ptr, cuda_stream):
+    """Whole-path solve that allocates nothing (see include/sgn.h): device pointers in and out, frame
+    texels in the library's fixed device scratch.  For callers that must not allocate device memory."""
+    _call("sgn_solve_static", ctypes.byref(desc), intrinsics_ptr, keyframe_ptr, keyframe_pitch_bytes, num_frames,
+          frame_ptrs_ptr, frame_pitch_bytes, poses_ptr, inv_depth0_ptr, normal0_ptr, state0_ptr, iters, inv_depth_ptr,
+          normal_ptr, cost_ptr, nres_ptr, status_ptr, depth_map_ptr, surfel_index_ptr, cuda_stream)
 
 
 def sgn_batch_create(max_plans) -> int:

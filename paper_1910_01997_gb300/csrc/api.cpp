@@ -122,6 +122,10 @@ sgn_status check_pose(const double* T) {
 
 namespace sgn {
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+sgn_status record_error(sgn_status st, const char* message) {
+    g_last_error = message;
+    return st;
+}
 }  // namespace sgn
 
 struct sgn_plan {

@@ -93,5 +93,7 @@ int batch_blocks_per_sm(int variant, int block_threads);
 int lanes_for_patch(int variant, int P);
 
 void count_launch(uint64_t n = 1);
+// Sets the calling thread's sgn_last_error() message and returns st.
+sgn_status record_error(sgn_status st, const char* message);
 
 }  // namespace sgn
