@@ -144,6 +144,7 @@ struct sgn_plan {
     double T[sgn::kMaxFrames][12] = {};
     int F = 0;
     bool surfels_set = false;
+    bool state_pending = false;  // initial surfels uploaded, working state not derived yet
     bool depth_valid = false;
     int lanes = 0, block = 256;
 };
@@ -524,12 +525,21 @@ sgn_status sgn_init_surfels(sgn_plan* p, const float* id, const float* n, const 
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.n0, n, 3 * S * sizeof(float), k, p->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.state0, state, S, k, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "surfel upload");
+    // The working state is derived from the initial surfels on first need (sgn_solve rebuilds it
+    // itself, so a solve right after the upload launches nothing extra).
+    p->surfels_set = true;
+    p->state_pending = true;
+    p->depth_valid = false;
+    return SGN_OK;
+}
+
+static sgn_status ensure_state(sgn_plan* p) {
+    if (!p->state_pending) return SGN_OK;
     PlanParams pp = make_params(p);
     int le = sgn::launch_init_state(pp, p->stream);
     if (le) return cuda_fail(le, "surfel initialisation launch");
     sgn::count_launch();
-    p->surfels_set = true;
-    p->depth_valid = false;
+    p->state_pending = false;
     return SGN_OK;
 }
 
@@ -543,6 +553,7 @@ sgn_status sgn_seed_surfels(sgn_plan* p) {
     int e = sgn::launch_seed(pp, p->stream);
     if (e) return cuda_fail(e, "seeding launch");
     sgn::count_launch();
+    p->state_pending = false;
     p->depth_valid = false;
     return SGN_OK;
 }
@@ -552,10 +563,12 @@ static sgn_status run_mode(sgn_plan* p, int iters, int mode) {
     if (st != SGN_OK) return st;
     if (iters < 0 || iters > 100000) return fail(SGN_ERR_INVALID_ARGUMENT, "iters %d outside [0, 100000]", iters);
     DeviceGuard g(p->device);
+    if (mode == sgn::kModeRun && (st = ensure_state(p)) != SGN_OK) return st;
     PlanParams pp = make_params(p);
     int e = sgn::launch_gn(pp, iters, mode, p->lanes, p->block, p->stream);
     if (e) return cuda_fail(e, "Gauss-Newton launch");
     sgn::count_launch();
+    p->state_pending = false;  // a solve writes the whole working state
     p->depth_valid = true;
     return SGN_OK;
 }
@@ -569,6 +582,7 @@ sgn_status sgn_read_surfels(sgn_plan* p, float* id, float* n, float* cost, int32
     if (!p->surfels_set) return fail(SGN_ERR_STATE, "surfels not initialised");
     if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
     DeviceGuard g(p->device);
+    if ((st = ensure_state(p)) != SGN_OK) return st;
     const size_t S = size_t(p->S);
     const cudaMemcpyKind k = kind_from_device(mem);
     cudaError_t e = cudaSuccess;
@@ -588,6 +602,7 @@ sgn_status sgn_read_depth_map(sgn_plan* p, float* inv_depth, int32_t* sidx, sgn_
     DeviceGuard g(p->device);
     if (!p->depth_valid) {
         if (!p->have_K || !p->surfels_set) return fail(SGN_ERR_STATE, "depth map needs intrinsics and surfels");
+        if ((st = ensure_state(p)) != SGN_OK) return st;
         PlanParams pp = make_params(p);
         int e = sgn::launch_render_depth(pp, p->stream);
         if (e) return cuda_fail(e, "depth render launch");
@@ -648,6 +663,7 @@ sgn_status sgn_import_state(sgn_plan* p, const void* host, size_t bytes) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.status, h + 24 * S, S, k, p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "state import");
     p->surfels_set = true;
+    p->state_pending = false;
     p->depth_valid = false;
     return sgn_sync(p, 0);
 }
@@ -839,7 +855,10 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
     if ((e = cudaEventRecord(b->done, b->stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     for (cudaStream_t s : streams)
         if ((e = cudaStreamWaitEvent(s, b->done, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
-    for (sgn_plan* p : b->plans) p->depth_valid = true;
+    for (sgn_plan* p : b->plans) {
+        p->depth_valid = true;
+        p->state_pending = false;
+    }
     return SGN_OK;
 }
 

@@ -40,7 +40,7 @@ __device__ __forceinline__ float stored(float v, int dtype) {
 }
 
 // Intensity + central-difference gradient (the grad I of Eq. 8), packed as one texel per pixel:
-// (I, gx, gy, 0).  The gradient is taken from the intensities as stored, so that with FP16/BF16
+// (gx, gy, I, 0).  The gradient is taken from the intensities as stored, so that with FP16/BF16
 // texels it is the exact central difference of the stored image (half the difference of two values
 // on the storage grid fits the storage mantissa).  Border rows/columns get a zero gradient; the
 // validity rule of the warp never samples them.
@@ -57,15 +57,15 @@ __global__ void __launch_bounds__(256) k_prep_frames(const __grid_constant__ Pre
     const float gy = (y >= 1 && y <= a.H - 2) ? 0.5f * (stored(__ldg(row + x + sp), dt) - stored(__ldg(row + x - sp), dt)) : 0.0f;
     const long long o = (long long)(a.first + f) * a.plane + (long long)y * a.tex_pitch + x;
     if (a.dtype == SGN_F32) {
-        static_cast<float4*>(a.dst)[o] = make_float4(I, gx, gy, 0.0f);
+        static_cast<float4*>(a.dst)[o] = make_float4(gx, gy, I, 0.0f);
     } else if (a.dtype == SGN_F16) {
-        __half2 lo = __floats2half2_rn(I, gx), hi = __floats2half2_rn(gy, 0.0f);
+        __half2 lo = __floats2half2_rn(gx, gy), hi = __floats2half2_rn(I, 0.0f);
         uint2 v;
         v.x = *reinterpret_cast<unsigned*>(&lo);
         v.y = *reinterpret_cast<unsigned*>(&hi);
         static_cast<uint2*>(a.dst)[o] = v;
     } else {
-        __nv_bfloat162 lo = __floats2bfloat162_rn(I, gx), hi = __floats2bfloat162_rn(gy, 0.0f);
+        __nv_bfloat162 lo = __floats2bfloat162_rn(gx, gy), hi = __floats2bfloat162_rn(I, 0.0f);
         uint2 v;
         v.x = *reinterpret_cast<unsigned*>(&lo);
         v.y = *reinterpret_cast<unsigned*>(&hi);
