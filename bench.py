@@ -136,6 +136,194 @@ def cpu_baseline(prob, budget_s: float = 10.0):
             "sample": f"{n} whole keyframe solves of the benchmark workload ({dt:.1f} s, FP64 C, OpenMP over surfels)"}
 
 
+def batch_leg(dtype: str, stream, dev, reps: int = 5):
+    """Config-4 leg: 64 keyframes of uneven size (320x240 .. 1920x1080, 4/8/16 px surfels, 2-8
+    frames), solved (a) one launch per keyframe, eager; (b) the same launches captured in one CUDA
+    graph; (c) one persistent batch launch with the autotuned schedule.  Returns residuals/s of each
+    and the distribution of inverse-depth differences between (c) and (a) (the two are compiled
+    separately, so chaotic surfels may round apart; parity is tested against the oracle)."""
+    import numpy as np
+    import torch
+
+    import paper_1910_01997_gb300 as sgn
+    import synth
+
+    probs = synth.batch_problems(0)
+    iters = WORKLOAD["iterations"]
+    plans, keep = [], []
+    with torch.cuda.stream(stream):
+        for pr in probs:
+            pl = sgn.Plan(pr.W, pr.H, pr.P, pr.F, dtype, stream=stream)
+            pl.set_intrinsics(*pr.cam)
+            kf = torch.from_numpy(pr.keyframe).to(dev)
+            fr = torch.from_numpy(pr.frames).to(dev)
+            pl.set_keyframe(kf)
+            pl.set_frames([fr[i] for i in range(pr.F)], pr.poses)
+            pl.init_surfels(pr.id0, pr.n0, pr.state)
+            plans.append(pl)
+            keep += [kf, fr]
+        stream.synchronize()
+        res = sum(pr.S * pr.P * pr.P * pr.F * iters for pr in probs)
+
+        def timed(fn):
+            fn()
+            stream.synchronize()
+            t = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                t.append(a.elapsed_time(b))
+            return statistics.median(t)
+
+        def plain():
+            for pl in plans:
+                pl.solve(iters)
+
+        ms_plain = timed(plain)
+        plain_out = [pl.read_surfels() for pl in plans]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            plain()
+        ms_graph = timed(g.replay)
+        batch = sgn.Batch(len(plans), stream=stream)
+        for pl in plans:
+            batch.add(pl)
+        variant, chunk = batch.autotune(iters)
+        ms_batch = timed(lambda: batch.run(iters))
+        diffs = []
+        for pl, ref in zip(plans, plain_out):
+            got = pl.read_surfels()
+            m = ((got["status"] & 0x3F) == 0) & ((ref["status"] & 0x3F) == 0)
+            diffs.append(np.abs(got["id"][m] / ref["id"][m] - 1))
+        diffs = np.concatenate(diffs)
+        batch.close()
+    S = [pr.S for pr in probs]
+    return {"texels": dtype, "keyframes": len(probs), "surfels_total": int(sum(S)), "surfels_min": int(min(S)),
+            "surfels_max": int(max(S)), "residuals_per_run": int(res),
+            "plain_eager": res / (ms_plain / 1e3), "plain_graph": res / (ms_graph / 1e3),
+            "batched": res / (ms_batch / 1e3), "speedup_vs_plain_graph": ms_graph / ms_batch,
+            "schedule": {"variant": variant, "surfels_per_item": chunk},
+            "depth_rel_diff_vs_plain": {"median": float(np.median(diffs)), "p99": float(np.percentile(diffs, 99)),
+                                        "frac_above_1e-4": float(np.mean(diffs > 1e-4))},
+            "unit": "residuals/s"}
+
+
+def serving_leg(duration_s: float, dev, streams: int = 16, rate_hz: float = 5.0, burst: int = 96):
+    """Config-5 leg: 16 simulated camera streams submit keyframe solves (Poisson arrivals, 5/s per
+    stream; half 640x480, half 1280x720; 8x8 surfels, 4 frames, FP16 texels, 10 iterations) to the
+    serving loop for duration_s seconds (open loop: per-keyframe latency p50/p99/max).  Then a burst
+    of requests measures saturated throughput, against plain per-keyframe upload + solve + readback
+    launches of the same requests on one stream."""
+    import numpy as np
+    import torch
+
+    import paper_1910_01997_gb300 as sgn
+    import synth
+
+    iters = WORKLOAD["iterations"]
+    pool = [synth.room_problem(300 + i, W=640, H=480, F=4) for i in range(4)] + \
+           [synth.room_problem(400 + i, W=1280, H=720, F=4) for i in range(4)]
+    pinned = []
+    for pr in pool:
+        pinned.append(dict(kf=torch.from_numpy(pr.keyframe).pin_memory(),
+                           frames=[torch.from_numpy(np.ascontiguousarray(f)).pin_memory() for f in pr.frames],
+                           id0=torch.from_numpy(pr.id0.astype(np.float32)).pin_memory(),
+                           n0=torch.from_numpy(pr.n0.astype(np.float32)).pin_memory(),
+                           st0=torch.from_numpy(pr.state).pin_memory()))
+    server = sgn.Server(16 << 30, max_slots=256, max_surfels_per_epoch=4_000_000)
+
+    def submit(k, tag):
+        pr, pi = pool[k], pinned[k]
+        return server.submit(pr.W, pr.H, pr.P, pr.cam, pi["kf"], pi["frames"], pr.poses, pi["id0"], pi["n0"], pi["st0"],
+                             iters, image_dtype="f16", tag=tag)
+
+    # warm-up
+    for k in range(len(pool)):
+        submit(k, 10_000_000 + k)
+    server.drain()
+    server.poll()
+    # open loop: merged Poisson schedule of the streams
+    rng = np.random.default_rng(7)
+    events = []
+    for st in range(streams):
+        t = rng.exponential(1.0 / rate_hz)
+        while t < duration_s:
+            events.append((t, st))
+            t += rng.exponential(1.0 / rate_hz)
+    events.sort()
+    base = server.stats()
+    done = []
+    t0 = time.perf_counter()
+    for i, (t, st) in enumerate(events):
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        k = (st % 4) + (0 if st < streams // 2 else 4)  # half the streams at 640x480, half at 1280x720
+        submit(k, i + 1)
+        if i % 16 == 15:
+            done += server.poll()
+    server.drain()
+    done += server.poll()
+    lat = [c.latency_ms for c, _ in done if 1 <= c.tag <= len(events) and c.status == sgn.SGN_OK]
+    assert len(lat) == len(events), (len(lat), len(events))
+    stats = server.stats()
+    wall = time.perf_counter() - t0
+    res_open = stats["residuals"] - base["residuals"]
+    # saturated: the same request mix submitted at once
+    sat_req = [(i % 8) for i in range(burst)]
+    res_burst = sum(pool[k].S * pool[k].P ** 2 * pool[k].F * iters for k in sat_req)
+    t1 = time.perf_counter()
+    for i, k in enumerate(sat_req):
+        submit(k, 20_000_000 + i)
+    server.drain()
+    t_served = time.perf_counter() - t1
+    server.poll()
+    server.close()
+    # plain: one plan per keyframe size, upload + solve + readback per request, one stream
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        plans = {}
+        outs = {}
+        for k in set(sat_req):
+            pr = pool[k]
+            plans[k] = sgn.Plan(pr.W, pr.H, pr.P, pr.F, "f16", stream=stream)
+            plans[k].set_intrinsics(*pr.cam)
+            outs[k] = [torch.empty(pr.S).pin_memory(), torch.empty(pr.S, 3).pin_memory(), torch.empty(pr.S).pin_memory(),
+                       torch.empty(pr.S, dtype=torch.int32).pin_memory(), torch.empty(pr.S, dtype=torch.uint8).pin_memory()]
+
+        def plain_one(k):
+            pr, pi, pl = pool[k], pinned[k], plans[k]
+            pl.set_keyframe(pi["kf"])
+            pl.set_frames(pi["frames"], pr.poses)
+            pl.init_surfels(pi["id0"], pi["n0"], pi["st0"])
+            pl.solve(iters)
+            sgn.sgn_read_surfels(pl.handle, *[t.data_ptr() for t in outs[k]], sgn.SGN_HOST)
+
+        for k in set(sat_req):
+            plain_one(k)
+        stream.synchronize()
+        t2 = time.perf_counter()
+        for k in sat_req:
+            plain_one(k)
+        stream.synchronize()
+        t_plain = time.perf_counter() - t2
+        for pl in plans.values():
+            pl._keep.clear()
+    lat = np.array(lat)
+    return {"streams": streams, "rate_per_stream_hz": rate_hz, "duration_s": duration_s, "requests": len(events),
+            "texels": "f16", "sizes": "half 640x480 (4800 surfels), half 1280x720 (14400 surfels); 8x8, 4 frames",
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max()), "mean": float(lat.mean())},
+            "offered_residuals_per_s": res_open / wall, "epochs": int(stats["epochs"] - base["epochs"]),
+            "saturated": {"requests": burst, "served_residuals_per_s": res_burst / t_served,
+                          "plain_residuals_per_s": res_burst / t_plain, "speedup": t_plain / t_served,
+                          "note": "host-to-device uploads, frame prep, solve and device-to-host results included in both"},
+            "unit": "residuals/s, ms"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -300,6 +488,10 @@ def run_ours(args):
         "kernel_ms_per_step": statistics.mean(kern_ms),
         "clocks": clk,
     }
+    if rank == 0 and not args.no_batch:
+        line["batch"] = [batch_leg(dt, stream, dev) for dt in ("f32", "f16")]
+    if rank == 0 and args.serve_seconds > 0:
+        line["serving"] = serving_leg(args.serve_seconds, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
     if rank == 0:
@@ -345,6 +537,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-keyframe batched leg")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="duration of the serving leg (0 skips it)")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written before each timed step")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

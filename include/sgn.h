@@ -219,6 +219,87 @@ sgn_status sgn_batch_run(sgn_batch* batch, int iters);
 sgn_status sgn_batch_sync(sgn_batch* batch, uint64_t timeout_ns);
 sgn_status sgn_batch_destroy(sgn_batch* batch);
 
+/* ---- serving: continuous batching of keyframe solves from many camera streams ------------ */
+
+typedef struct sgn_server sgn_server;   /* opaque, host side */
+
+/* One keyframe solve request.  All pointers are host memory (page-locked memory makes the copies
+ * asynchronous) and must stay valid until the request's completion is returned by sgn_server_poll;
+ * desc/intrinsics/poses/frames[] (the pointer array) are copied at submission. */
+typedef struct {
+    sgn_plan_desc desc;          /* size, patch, frame slots, texel type, options */
+    double intrinsics[4];        /* fx, fy, cx, cy */
+    const float* keyframe;       /* W x H, tightly packed */
+    int num_frames;              /* 1..desc.max_frames */
+    const float* const* frames;  /* num_frames pointers to W x H images */
+    const double* poses;         /* 12 per frame, keyframe -> frame */
+    const float* inv_depth0;     /* initial surfels as in sgn_init_surfels */
+    const float* normal0;
+    const uint8_t* state0;
+    int iters;                   /* Gauss-Newton iterations (sgn_solve) */
+    float* inv_depth;            /* results as in sgn_read_surfels (S, 3 S, S, S, S) */
+    float* normal;
+    float* cost;
+    int32_t* nres;
+    uint8_t* status;
+    uint64_t tag;                /* caller's identifier, returned in the completion */
+} sgn_request;
+
+typedef struct {
+    uint64_t tag;
+    sgn_status status;   /* SGN_OK, SGN_ERR_CUDA, SGN_ERR_STATE (cancelled) ... */
+    int cancelled;
+    double latency_ms;   /* submission -> results in host memory */
+    double queue_ms;     /* submission -> admission */
+} sgn_completion;
+
+typedef struct {
+    uint64_t completed, epochs, rejected, admission_waits, residuals;
+    size_t peak_arena_bytes;
+    double latency_p50_ms, latency_p99_ms, latency_max_ms, latency_mean_ms;
+    double busy_seconds; /* first submission -> last completion */
+} sgn_serving_stats;
+
+/* Start a server over a caller-owned device arena (256-byte aligned) that bounds the device memory
+ * of the requests in flight (admission by free memory): each admitted request takes its plan
+ * workspace (sgn_plan_workspace_bytes) from the arena until it completes; a request larger than the
+ * arena is refused at submission with SGN_ERR_ADMISSION, one that does not fit yet waits.
+ * compute_stream runs the batched solves, copy_stream the uploads, frame preparation and result
+ * copies (two distinct non-default streams of the current device).  An epoch = one persistent batch
+ * launch over every request uploaded since the previous launch, at most max_slots requests and
+ * max_surfels_per_epoch surfels (plus one work item per request); up to two epochs are in flight.
+ * A server thread makes all CUDA calls. */
+sgn_status sgn_server_create(void* d_arena, size_t arena_bytes, int max_slots, int max_surfels_per_epoch,
+                             void* compute_stream, void* copy_stream, sgn_server** out);
+/* Queue a request (thread-safe; no CUDA call in the caller's thread). */
+sgn_status sgn_server_submit(sgn_server* server, const sgn_request* request);
+/* Cancel by tag: a request not yet finished completes with cancelled = 1 (its results are not
+ * written if it had not run yet; if it already ran, they may be). */
+sgn_status sgn_server_cancel(sgn_server* server, uint64_t tag);
+/* Take up to max completions (in completion order). */
+sgn_status sgn_server_poll(sgn_server* server, sgn_completion* out, int max, int* n);
+/* Wait until every submitted request has completed; timeout_ns = 0 waits forever. */
+sgn_status sgn_server_drain(sgn_server* server, uint64_t timeout_ns);
+sgn_status sgn_server_stats(sgn_server* server, sgn_serving_stats* out);
+/* Finish the requests in flight, then stop the server thread. */
+sgn_status sgn_server_destroy(sgn_server* server);
+
+/* ---- autotuning -------------------------------------------------------------------------- */
+
+/* Choose the plan's kernel mapping (lanes per surfel x threads per block, as in
+ * sgn_plan_set_mapping) by timing sgn_solve(plan, iters) for every supported mapping on the bound
+ * stream (one warm-up and three timed runs each; the plan is left with the working state of a
+ * solve).  cache_path (may be NULL) names a text file of earlier results keyed by GPU name and
+ * problem shape; a hit skips the timing, a miss appends a line.  Synchronises the stream. */
+sgn_status sgn_plan_autotune(sgn_plan* plan, int iters, const char* cache_path, int* lanes_per_surfel,
+                             int* block_threads);
+
+/* Choose the batch schedule (variant x surfels per work item, as in sgn_batch_set_schedule) by
+ * timing sgn_batch_run(batch, iters) for variants {0, 1} x chunks {8, 16, 32, 64, 128, 256}.
+ * Schedules whose work list does not fit the bound workspace are skipped: bind a workspace sized
+ * at chunk 8 to try them all.  Cache as for sgn_plan_autotune. */
+sgn_status sgn_batch_autotune(sgn_batch* batch, int iters, const char* cache_path, int* variant, int* chunk);
+
 /* ---- introspection --------------------------------------------------------------------- */
 
 /* Message for the calling thread's last failed call ("" if none). */

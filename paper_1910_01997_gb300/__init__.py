@@ -42,6 +42,28 @@ class sgn_plan_desc(ctypes.Structure):
                 ("min_residuals", ctypes.c_int)]
 
 
+class sgn_request(ctypes.Structure):
+    _fields_ = [("desc", sgn_plan_desc), ("intrinsics", ctypes.c_double * 4), ("keyframe", ctypes.c_void_p),
+                ("num_frames", ctypes.c_int), ("frames", ctypes.c_void_p), ("poses", ctypes.c_void_p),
+                ("inv_depth0", ctypes.c_void_p), ("normal0", ctypes.c_void_p), ("state0", ctypes.c_void_p),
+                ("iters", ctypes.c_int), ("inv_depth", ctypes.c_void_p), ("normal", ctypes.c_void_p),
+                ("cost", ctypes.c_void_p), ("nres", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("tag", ctypes.c_uint64)]
+
+
+class sgn_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int), ("cancelled", ctypes.c_int),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+
+
+class sgn_serving_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("epochs", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("admission_waits", ctypes.c_uint64), ("residuals", ctypes.c_uint64),
+                ("peak_arena_bytes", ctypes.c_size_t), ("latency_p50_ms", ctypes.c_double),
+                ("latency_p99_ms", ctypes.c_double), ("latency_max_ms", ctypes.c_double),
+                ("latency_mean_ms", ctypes.c_double), ("busy_seconds", ctypes.c_double)]
+
+
 class SgnError(RuntimeError):
     def __init__(self, status: int, func: str):
         self.status = status
@@ -77,6 +99,15 @@ _SIGS = {
     "sgn_import_state": [_P, _P, _SZ],
     "sgn_solve_static": [ctypes.POINTER(sgn_plan_desc), _P, _P, _SZ, _I, _P, _SZ, _P, _P, _P, _P, _I,
                          _P, _P, _P, _P, _P, _P, _P, _P],
+    "sgn_plan_autotune": [_P, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "sgn_server_create": [_P, _SZ, _I, _I, _P, _P, ctypes.POINTER(_P)],
+    "sgn_server_submit": [_P, ctypes.POINTER(sgn_request)],
+    "sgn_server_cancel": [_P, ctypes.c_uint64],
+    "sgn_server_poll": [_P, ctypes.POINTER(sgn_completion), _I, ctypes.POINTER(_I)],
+    "sgn_server_drain": [_P, ctypes.c_uint64],
+    "sgn_server_stats": [_P, ctypes.POINTER(sgn_serving_stats)],
+    "sgn_server_destroy": [_P],
+    "sgn_batch_autotune": [_P, _I, ctypes.c_char_p, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "sgn_batch_create": [_I, ctypes.POINTER(_P)],
     "sgn_batch_add": [_P, _P],
     "sgn_batch_clear": [_P],
@@ -224,6 +255,20 @@ def sgn_solve_static(desc, intrinsics_ptr, keyframe_ptr, keyframe_pitch_bytes, n
           normal_ptr, cost_ptr, nres_ptr, status_ptr, depth_map_ptr, surfel_index_ptr, cuda_stream)
 
 
+def sgn_plan_autotune(plan, iters, cache_path=None):
+    a, b = _I(), _I()
+    _call("sgn_plan_autotune", plan, int(iters), None if cache_path is None else str(cache_path).encode(),
+          ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def sgn_batch_autotune(batch, iters, cache_path=None):
+    a, b = _I(), _I()
+    _call("sgn_batch_autotune", batch, int(iters), None if cache_path is None else str(cache_path).encode(),
+          ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
 def sgn_batch_create(max_plans) -> int:
     h = _P()
     _call("sgn_batch_create", max_plans, ctypes.byref(h))
@@ -262,6 +307,42 @@ def sgn_batch_sync(batch, timeout_ns=0):
 
 def sgn_batch_destroy(batch):
     _call("sgn_batch_destroy", batch)
+
+
+def sgn_server_create(d_arena, arena_bytes, max_slots, max_surfels_per_epoch, compute_stream, copy_stream) -> int:
+    h = _P()
+    _call("sgn_server_create", d_arena, arena_bytes, max_slots, max_surfels_per_epoch, compute_stream, copy_stream,
+          ctypes.byref(h))
+    return h.value
+
+
+def sgn_server_submit(server, request: sgn_request):
+    _call("sgn_server_submit", server, ctypes.byref(request))
+
+
+def sgn_server_cancel(server, tag):
+    _call("sgn_server_cancel", server, tag)
+
+
+def sgn_server_poll(server, max_n=1024):
+    buf = (sgn_completion * max_n)()
+    n = _I()
+    _call("sgn_server_poll", server, buf, max_n, ctypes.byref(n))
+    return [buf[i] for i in range(n.value)]
+
+
+def sgn_server_drain(server, timeout_ns=0):
+    _call("sgn_server_drain", server, timeout_ns)
+
+
+def sgn_server_stats(server) -> sgn_serving_stats:
+    st = sgn_serving_stats()
+    _call("sgn_server_stats", server, ctypes.byref(st))
+    return st
+
+
+def sgn_server_destroy(server):
+    _call("sgn_server_destroy", server)
 
 
 def sgn_last_error() -> str:
@@ -376,6 +457,10 @@ class Plan:
     def set_num_frames(self, n):
         sgn_set_num_frames(self.handle, n)
 
+    def autotune(self, iters, cache_path=None):
+        """Time the supported kernel mappings of sgn_solve and keep the fastest (C++ autotuner)."""
+        return sgn_plan_autotune(self.handle, iters, cache_path)
+
     def init_surfels(self, inv_depth, normal, state):
         torch = _torch()
         a = _as(inv_depth, np.float32, torch.float32)
@@ -475,9 +560,99 @@ class Batch:
     def sync(self, timeout_ns=0):
         sgn_batch_sync(self.handle, timeout_ns)
 
+    def autotune(self, iters, cache_path=None):
+        """Bind a workspace large enough for every schedule, then time the schedules (C++ autotuner)."""
+        sgn_batch_set_schedule(self.handle, 0, 8)
+        self._bind()
+        return sgn_batch_autotune(self.handle, iters, cache_path)
+
     def close(self):
         if getattr(self, "handle", None):
             sgn_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A serving loop over a torch-allocated device arena, with its own compute and copy streams.
+
+    submit() takes host inputs (numpy or page-locked torch CPU tensors) and returns the tag; the
+    request's output arrays are allocated page-locked here and returned by poll() together with the
+    completion record once the request has finished."""
+
+    def __init__(self, arena_bytes, max_slots=256, max_surfels_per_epoch=2_000_000):
+        torch = _torch()
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+        self.compute = torch.cuda.Stream()
+        self.copy = torch.cuda.Stream()
+        self.handle = sgn_server_create(self.arena.data_ptr(), int(arena_bytes), max_slots, max_surfels_per_epoch,
+                                        self.compute.cuda_stream, self.copy.cuda_stream)
+        self._live = {}
+        self._next = 1
+
+    def submit(self, W, H, P, cam, keyframe, frames, poses, id0, n0, state, iters, image_dtype="f32",
+               max_frames=None, tag=None, **opts):
+        torch = _torch()
+        F = len(frames)
+        d = sgn_plan_desc_default(W, H, P, max_frames or F)
+        d.image_dtype = DTYPES[image_dtype] if isinstance(image_dtype, str) else int(image_dtype)
+        for k, v in opts.items():
+            setattr(d, k, v)
+        S = (W // P) * (H // P)
+
+        def pinned(a, dtype):
+            if isinstance(a, torch.Tensor):
+                return a.contiguous()
+            return torch.from_numpy(np.ascontiguousarray(a, dtype=dtype)).pin_memory()
+
+        ins = dict(kf=pinned(keyframe, np.float32), frames=[pinned(f, np.float32) for f in frames],
+                   id0=pinned(id0, np.float32), n0=pinned(n0, np.float32), st0=pinned(state, np.uint8))
+        outs = dict(id=torch.empty(S).pin_memory(), n=torch.empty(S, 3).pin_memory(), cost=torch.empty(S).pin_memory(),
+                    nres=torch.empty(S, dtype=torch.int32).pin_memory(), status=torch.empty(S, dtype=torch.uint8).pin_memory())
+        fptrs = (ctypes.c_void_p * F)(*[f.data_ptr() for f in ins["frames"]])
+        T = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(F, 12))
+        if tag is None:
+            tag = self._next
+            self._next += 1
+        r = sgn_request()
+        r.desc = d
+        for i, c in enumerate(cam):
+            r.intrinsics[i] = float(c)
+        r.keyframe, r.num_frames, r.frames, r.poses = ins["kf"].data_ptr(), F, ctypes.cast(fptrs, ctypes.c_void_p).value, T.ctypes.data
+        r.inv_depth0, r.normal0, r.state0 = ins["id0"].data_ptr(), ins["n0"].data_ptr(), ins["st0"].data_ptr()
+        r.iters = int(iters)
+        r.inv_depth, r.normal, r.cost = outs["id"].data_ptr(), outs["n"].data_ptr(), outs["cost"].data_ptr()
+        r.nres, r.status, r.tag = outs["nres"].data_ptr(), outs["status"].data_ptr(), tag
+        self._live[tag] = (ins, outs, fptrs, T, r)
+        sgn_server_submit(self.handle, r)
+        return tag
+
+    def cancel(self, tag):
+        sgn_server_cancel(self.handle, tag)
+
+    def poll(self):
+        """[(completion, outputs as numpy arrays)] of requests finished since the last poll."""
+        out = []
+        for c in sgn_server_poll(self.handle):
+            ins, outs, *_ = self._live.pop(c.tag)
+            out.append((c, {k: v.numpy().copy() for k, v in outs.items()}))
+        return out
+
+    def drain(self, timeout_ns=0):
+        sgn_server_drain(self.handle, timeout_ns)
+
+    def stats(self):
+        st = sgn_server_stats(self.handle)
+        return {f: getattr(st, f) for f, _ in sgn_serving_stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sgn_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <sstream>
 #include <string>
 #include <thread>
 #include <vector>
@@ -884,3 +885,38 @@ uint64_t sgn_launch_count(void) { return g_launches.load(std::memory_order_relax
 int sgn_abi_version(void) { return SGN_ABI_VERSION; }
 
 }  // extern "C"
+
+namespace sgn {
+PlanParams plan_params(const sgn_plan* p) { return make_params(p); }
+bool plan_ready(const sgn_plan* p) { return require_ready(p) == SGN_OK; }
+// After a batched solve of this plan: the working state and depth map are those of a solve.
+void plan_mark_solved(sgn_plan* p) {
+    p->state_pending = false;
+    p->depth_valid = true;
+}
+cudaStream_t plan_stream(const sgn_plan* p) { return p->stream; }
+void plan_shape(const sgn_plan* p, int* W, int* H, int* P, int* F, int* dtype) {
+    *W = p->desc.width;
+    *H = p->desc.height;
+    *P = p->desc.patch;
+    *F = p->F;
+    *dtype = p->desc.image_dtype;
+}
+cudaStream_t batch_stream(const sgn_batch* b) { return b->stream; }
+// Shape of a batch for tuning caches: plan count and a hash of the (W, H, P, F, dtype) multiset.
+std::string batch_signature(const sgn_batch* b) {
+    std::vector<std::string> shapes;
+    for (const sgn_plan* p : b->plans) {
+        std::ostringstream o;
+        o << p->desc.width << 'x' << p->desc.height << 'p' << p->desc.patch << 'f' << p->F << 'd' << p->desc.image_dtype;
+        shapes.push_back(o.str());
+    }
+    std::sort(shapes.begin(), shapes.end());
+    uint64_t h = 1469598103934665603ull;  // FNV-1a
+    for (const std::string& s : shapes)
+        for (char c : s + ";") h = (h ^ uint8_t(c)) * 1099511628211ull;
+    std::ostringstream o;
+    o << b->plans.size() << "plans-" << std::hex << h;
+    return o.str();
+}
+}  // namespace sgn

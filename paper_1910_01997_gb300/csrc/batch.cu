@@ -43,7 +43,7 @@ __device__ __forceinline__ void dispatch_patch(const PlanParams* pp, const WorkI
 }
 
 template <int V>
-__global__ void __launch_bounds__(kBatchBlock) k_gn_batch(const PlanParams* __restrict__ plans,
+__global__ void __launch_bounds__(kBatchBlock, 2) k_gn_batch(const PlanParams* __restrict__ plans,
                                                           const WorkItem* __restrict__ items, int n_items,
                                                           int* __restrict__ counter, int iters) {
     __shared__ PlanParams spp[kBatchWarps];

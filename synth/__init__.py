@@ -316,34 +316,34 @@ class Problem:
         return self.S * self.P * self.P * self.F
 
 
-def _rotate_perturb(n, max_deg, rng):
-    a = rng.normal(size=3)
-    a -= (a @ n) * n
-    a /= np.linalg.norm(a)
-    return rot_axis_angle(a, np.deg2rad(rng.uniform(0, max_deg))) @ n
+def render_set(scene: Scene, noise_sigma: float, seed: int, idx: list) -> dict:
+    """Noisy renders {camera index: (image, primitive ids)} for the given cameras (0 = keyframe)."""
+    out = {}
+    for i in idx:
+        nz = None
+        if noise_sigma > 0:
+            nz = np.random.default_rng([seed, 4, i]).normal(0.0, noise_sigma, size=(scene.H, scene.W))
+        img, pid, _ = scene.render(i, nz)
+        out[i] = (img, pid)
+    return out
 
 
 def make_problem(scene: Scene, P: int, *, noise_sigma: float = 0.0, seed_frac: float = 0.0,
                  depth_perturb: float = 0.1, normal_perturb_deg: float = 10.0, seed: int = 0,
-                 frames: list | None = None) -> Problem:
+                 frames: list | None = None, rendered: dict | None = None, init_seed: int | None = None) -> Problem:
     """Render the keyframe and observing frames and draw the initial surfels.
 
     Valid tiles start from ground truth with inverse depth scaled by U[1-d, 1+d] and the
     normal rotated by U[0, normal_perturb_deg] about a random perpendicular axis.  A
     ``seed_frac`` share of tiles (seeded choice) is marked TO_SEED instead.
     """
-    rng = np.random.default_rng([seed, 3])
+    rng = np.random.default_rng([seed if init_seed is None else init_seed, 3])
     W, H = scene.W, scene.H
     idx = list(range(1, len(scene.poses))) if frames is None else list(frames)
-
-    def noisy(i):
-        nz = None
-        if noise_sigma > 0:
-            nz = np.random.default_rng([seed, 4, i]).normal(0.0, noise_sigma, size=(H, W))
-        return scene.render(i, nz)
-
-    kf, kf_pid, _ = noisy(0)
-    fr = np.stack([noisy(i)[0] for i in idx])
+    if rendered is None:
+        rendered = render_set(scene, noise_sigma, seed, [0] + idx)
+    kf, kf_pid = rendered[0]
+    fr = np.stack([rendered[i][0] for i in idx])
     poses = np.stack([scene.poses[i] for i in idx])
     TX, TY = W // P, H // P
     S = TX * TY
@@ -368,14 +368,19 @@ def make_problem(scene: Scene, P: int, *, noise_sigma: float = 0.0, seed_frac: f
         state[pick] = np.where(state[pick] == VALID, TO_SEED, state[pick])
     id0 = np.zeros(S)
     n0 = np.zeros((S, 3))
-    for s in range(S):
-        if state[s] != VALID:
-            continue
-        id0[s] = gt_id[s] * (1.0 + rng.uniform(-depth_perturb, depth_perturb))
-        n = gt_n[s] if normal_perturb_deg == 0 else _rotate_perturb(gt_n[s], normal_perturb_deg, rng)
-        if n @ rays[s] > 0:
-            n = -n
-        n0[s] = n
+    v = state == VALID
+    nv = int(v.sum())
+    id0[v] = gt_id[v] * (1.0 + rng.uniform(-depth_perturb, depth_perturb, nv))
+    # rotate each normal by U[0, max] degrees about a random axis perpendicular to it (Rodrigues)
+    axis = rng.normal(size=(nv, 3))
+    g = gt_n[v]
+    axis -= np.einsum("ij,ij->i", axis, g)[:, None] * g
+    axis /= np.linalg.norm(axis, axis=1, keepdims=True)
+    ang = np.deg2rad(rng.uniform(0.0, normal_perturb_deg, nv))
+    n = g * np.cos(ang)[:, None] + np.cross(axis, g) * np.sin(ang)[:, None]
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    n[np.einsum("ij,ij->i", n, rays[v]) > 0] *= -1
+    n0[v] = n
     return Problem(W=W, H=H, P=P, cam=scene.cam.copy(), keyframe=kf, frames=fr, poses=poses, id0=id0,
                    n0=n0, state=state, gt_id=gt_id, gt_n=gt_n, tile_prim=tile_prim, scene=scene,
                    frame_index=idx, noise_sigma=noise_sigma)
@@ -429,3 +434,26 @@ def ring_scene(seed: int, W: int = 320, H: int = 240, n_frames: int = 6, radius:
 
 def ring_problem(seed: int = 0, P: int = 16, noise_sigma: float = 0.0, **kw) -> Problem:
     return make_problem(ring_scene(seed), P, noise_sigma=noise_sigma, seed=seed, **kw)
+
+
+def batch_problems(seed: int = 0, n: int = 64, scenes: int = 16, max_frames: int = 8) -> list:
+    """Many keyframe problems of uneven size for batched execution: resolutions drawn from
+    {320x240, 640x480, 1280x720, 1920x1080}, patch sizes from {4, 8, 16}, 2..max_frames observing
+    frames, 20 % seeded tiles, noise sigma 0.01.  `scenes` box-room scenes are rendered once (with
+    max_frames observing frames) and shared by the n problems, which differ in patch size, frame
+    count, seeded tiles and initial perturbation."""
+    rng = np.random.default_rng([seed, 6])
+    sizes = [(320, 240), (640, 480), (1280, 720), (1920, 1080)]
+    scene_list = []
+    for k in range(scenes):
+        W, H = sizes[k % len(sizes)]
+        sc = room_scene(1000 + 31 * seed + k, W, H, max_frames)
+        scene_list.append((sc, render_set(sc, 0.01, 1000 + k, list(range(max_frames + 1)))))
+    out = []
+    for j in range(n):
+        sc, rendered = scene_list[int(rng.integers(len(scene_list)))]
+        P = int(rng.choice([4, 8, 16]))
+        F = int(rng.integers(2, max_frames + 1))
+        out.append(make_problem(sc, P, noise_sigma=0.01, seed_frac=0.2, seed=1000 + j, frames=list(range(1, F + 1)),
+                                rendered=rendered, init_seed=5000 + j))
+    return out

@@ -1,0 +1,111 @@
+"""Serving loop: continuous batching of keyframe solves submitted from many streams.  A request's
+result is the same alone and in a mix; results match the oracle; admission by free device memory
+queues what does not fit and refuses what never can; cancellation and drain deadlines work."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import gpu_solve, oracle_solve, oracle_solve_planes, stored_planes
+
+pytestmark = pytest.mark.gpu
+
+
+def _submit(server, prob, dtype="f32", tag=None, iters=10):
+    return server.submit(prob.W, prob.H, prob.P, prob.cam, prob.keyframe, list(prob.frames), prob.poses, prob.id0,
+                         prob.n0, prob.state, iters, image_dtype=dtype, tag=tag)
+
+
+def _collect(server):
+    server.drain(30_000_000_000)
+    return {c.tag: (c, out) for c, out in server.poll()}
+
+
+def _mix():
+    return [synth.room_problem(20 + i, W=[320, 640][i % 2], H=[240, 480][i % 2], F=2 + i % 4, P=[8, 16, 4][i % 3])
+            for i in range(8)]
+
+
+def test_result_alone_equals_result_in_a_mix():
+    import paper_1910_01997_gb300 as sgn
+
+    probe = synth.room_problem(40, F=4)
+    server = sgn.Server(2 << 30)
+    _submit(server, probe, tag=1)
+    alone = _collect(server)[1][1]
+    tags = {}
+    for i, p in enumerate(_mix()):
+        tags[100 + i] = _submit(server, p, dtype=["f32", "f16"][i % 2], tag=100 + i)
+    _submit(server, probe, tag=2)
+    for i, p in enumerate(_mix()[:3]):
+        _submit(server, p, tag=200 + i)
+    done = _collect(server)
+    assert all(c.status == sgn.SGN_OK for c, _ in done.values())
+    mixed = done[2][1]
+    for k in ("id", "n", "cost", "nres", "status"):
+        assert np.array_equal(alone[k], mixed[k]), k
+    st = server.stats()
+    assert st["completed"] == 13 and st["epochs"] >= 2
+    server.close()
+
+
+def test_served_results_match_the_oracle():
+    import paper_1910_01997_gb300 as sgn
+    from test_gpu_parity import _check
+
+    probs = [("f32", synth.room_problem(41)), ("f16", synth.room_problem(42, F=4))]
+    server = sgn.Server(2 << 30)
+    for i, (dt, p) in enumerate(probs):
+        _submit(server, p, dtype=dt, tag=i + 1)
+    done = _collect(server)
+    for i, (dt, p) in enumerate(probs):
+        c, got = done[i + 1]
+        assert c.status == sgn.SGN_OK and c.latency_ms > 0
+        if dt == "f32":
+            _check(p, got, oracle_solve(p, 10), "f32", "served f32", 10)
+        else:
+            planes = stored_planes(p.frames, dt)
+            _check(p, got, oracle_solve_planes(p, planes, 10), "f32", "served f16 vs planes", 10, planes=planes)
+    server.close()
+
+
+def test_admission_by_free_memory():
+    import paper_1910_01997_gb300 as sgn
+
+    p = synth.room_problem(43, W=320, H=240, F=3)
+    h = sgn.sgn_plan_create(sgn.sgn_plan_desc_default(p.W, p.H, p.P, p.F))
+    need = sgn.sgn_plan_workspace_bytes(h)
+    sgn.sgn_plan_destroy(h)
+    server = sgn.Server(int(1.5 * need) + (8 << 20), max_slots=4, max_surfels_per_epoch=20000)
+    for i in range(4):
+        _submit(server, p, tag=10 + i)
+    done = _collect(server)
+    assert sorted(done) == [10, 11, 12, 13] and all(c.status == sgn.SGN_OK for c, _ in done.values())
+    st = server.stats()
+    assert st["admission_waits"] > 0 and st["peak_arena_bytes"] <= int(1.5 * need) + (8 << 20)
+    ref = gpu_solve(p, 10)
+    m = ((done[10][1]["status"] & 0x3F) == 0) & ((ref["status"] & 0x3F) == 0)
+    assert np.median(np.abs(done[10][1]["id"][m] / ref["id"][m] - 1)) < 1e-6
+    big = synth.room_problem(44)  # 640x480: more than the whole arena
+    with pytest.raises(sgn.SgnError) as e:
+        _submit(server, big, tag=99)
+    assert e.value.status == sgn.SGN_ERR_ADMISSION and server.stats()["rejected"] == 1
+    server.close()
+
+
+def test_cancel_and_drain_deadline():
+    import paper_1910_01997_gb300 as sgn
+
+    p = synth.room_problem(45, W=320, H=240, F=3)
+    h = sgn.sgn_plan_create(sgn.sgn_plan_desc_default(p.W, p.H, p.P, p.F))
+    need = sgn.sgn_plan_workspace_bytes(h)
+    sgn.sgn_plan_destroy(h)
+    server = sgn.Server(need + (8 << 20), max_slots=4, max_surfels_per_epoch=20000)  # one request at a time
+    for i in range(3):
+        _submit(server, p, tag=1 + i, iters=200)
+    server.cancel(3)
+    st = sgn._status("sgn_server_drain", server.handle, 1)
+    assert st in (sgn.SGN_ERR_TIMEOUT, sgn.SGN_OK)
+    done = _collect(server)
+    assert done[3][0].cancelled == 1 and done[3][0].status == sgn.SGN_ERR_STATE
+    assert done[1][0].status == sgn.SGN_OK and done[2][0].status == sgn.SGN_OK
+    server.close()
