@@ -302,6 +302,14 @@ sgn_status sgn_batch_autotune(sgn_batch* batch, int iters, const char* cache_pat
 
 /* ---- introspection --------------------------------------------------------------------- */
 
+/* Diagnostic (no counterpart in the paper): r[i] = 1 / x[i] for n values, computed exactly as the
+ * FP64 normal-equation solve computes its pivot reciprocals (hardware estimate plus a series
+ * correction), so that tests can compare it with IEEE division.  x and r are device pointers to n
+ * doubles (they may alias); every x[i] must be a positive normal double.  Enqueued on `stream`
+ * (cudaStream_t, may be NULL); n = 0 is a no-op; NULL pointers with n > 0 or n < 0 give
+ * SGN_ERR_INVALID_ARGUMENT. */
+sgn_status sgn_check_fp64_reciprocal(const double* x, double* r, int n, void* stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* sgn_last_error(void);
 

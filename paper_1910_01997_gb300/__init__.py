@@ -117,6 +117,7 @@ _SIGS = {
     "sgn_batch_run": [_P, _I],
     "sgn_batch_sync": [_P, ctypes.c_uint64],
     "sgn_batch_destroy": [_P],
+    "sgn_check_fp64_reciprocal": [_P, _P, _I, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -355,6 +356,19 @@ def sgn_launch_count() -> int:
 
 def sgn_abi_version() -> int:
     return int(_lib.sgn_abi_version())
+
+
+def sgn_check_fp64_reciprocal(x, stream=None):
+    """Reciprocals of the positive FP64 CUDA tensor x as the FP64 solve computes them (diagnostic)."""
+    import torch
+
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise ValueError("x must be a contiguous float64 CUDA tensor")
+    r = torch.empty_like(x)
+    s = torch.cuda.current_stream() if stream is None else stream
+    _call("sgn_check_fp64_reciprocal", x.data_ptr(), r.data_ptr(), x.numel(), s.cuda_stream)
+    s.synchronize()
+    return r
 
 
 # ------------------------------------------------------------------------------- helpers
