@@ -300,6 +300,21 @@ sgn_status sgn_plan_autotune(sgn_plan* plan, int iters, const char* cache_path, 
  * at chunk 8 to try them all.  Cache as for sgn_plan_autotune. */
 sgn_status sgn_batch_autotune(sgn_batch* batch, int iters, const char* cache_path, int* variant, int* chunk);
 
+/* Shared-memory staging of frame texels (default off).  With staging, each surfel's Gauss-Newton
+ * evaluation reads the bilinear taps from boxes of texels around the projection of its tile centre,
+ * copied into shared memory by the tensor memory accelerator two boxes ahead of use; taps outside a
+ * box read global memory.  Results are identical with and without staging (same texels, same
+ * arithmetic); it changes only where the taps come from.  Without staging the taps are read through
+ * the L1 cache, which keeps a surfel's footprint across iterations, whereas the boxes are fetched
+ * again on every pass; on one GB300 at 640x480 staging is the slower of the two.  enabled: 1 or 0. */
+sgn_status sgn_plan_set_staging(sgn_plan* plan, int enabled);
+
+/* Number of staging waits on the current device that ran out of time (about one second each) since
+ * the library was loaded.  A surfel whose wait runs out reads its texels from global memory for
+ * the rest of the launch, so results stay correct; a non-zero count means the GPU stalled.
+ * Synchronous (a 4-byte device-to-host copy). */
+sgn_status sgn_staging_timeouts(uint32_t* count);
+
 /* ---- introspection --------------------------------------------------------------------- */
 
 /* Diagnostic (no counterpart in the paper): r[i] = 1 / x[i] for n values, computed exactly as the

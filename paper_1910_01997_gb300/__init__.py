@@ -118,6 +118,8 @@ _SIGS = {
     "sgn_batch_sync": [_P, ctypes.c_uint64],
     "sgn_batch_destroy": [_P],
     "sgn_check_fp64_reciprocal": [_P, _P, _I, _P],
+    "sgn_plan_set_staging": [_P, _I],
+    "sgn_staging_timeouts": [ctypes.POINTER(ctypes.c_uint32)],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -175,6 +177,10 @@ def sgn_plan_workspace_bytes(plan) -> int:
 
 def sgn_plan_set_mapping(plan, lanes_per_surfel, block_threads):
     _call("sgn_plan_set_mapping", plan, lanes_per_surfel, block_threads)
+
+
+def sgn_plan_set_staging(plan, enabled):
+    _call("sgn_plan_set_staging", plan, int(enabled))
 
 
 def sgn_plan_bind(plan, d_workspace, nbytes, cuda_stream):
@@ -358,6 +364,12 @@ def sgn_abi_version() -> int:
     return int(_lib.sgn_abi_version())
 
 
+def sgn_staging_timeouts() -> int:
+    n = ctypes.c_uint32()
+    _call("sgn_staging_timeouts", ctypes.byref(n))
+    return int(n.value)
+
+
 def sgn_check_fp64_reciprocal(x, stream=None):
     """Reciprocals of the positive FP64 CUDA tensor x as the FP64 solve computes them (diagnostic)."""
     import torch
@@ -405,7 +417,7 @@ class Plan:
 
     def __init__(self, width, height, patch, max_frames, image_dtype="f32", *, huber_k=9.0 / 255.0,
                  lm_lambda=1e-3, fp64_cond=1e6, optimize_normal=True, min_residuals=8, stream=None,
-                 lanes_per_surfel=0, block_threads=0):
+                 lanes_per_surfel=0, block_threads=0, staging=False):
         torch = _torch()
         d = sgn_plan_desc_default(width, height, patch, max_frames)
         d.image_dtype = DTYPES[image_dtype] if isinstance(image_dtype, str) else int(image_dtype)
@@ -417,6 +429,8 @@ class Plan:
         self.S = sgn_plan_num_surfels(self.handle)
         if lanes_per_surfel or block_threads:
             sgn_plan_set_mapping(self.handle, lanes_per_surfel, block_threads)
+        if staging:
+            sgn_plan_set_staging(self.handle, 1)
         nbytes = sgn_plan_workspace_bytes(self.handle)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream()

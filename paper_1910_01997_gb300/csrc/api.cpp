@@ -148,6 +148,9 @@ struct sgn_plan {
     bool state_pending = false;  // initial surfels uploaded, working state not derived yet
     bool depth_valid = false;
     int lanes = 0, block = 256;
+    bool staging = false;                 // stage texel boxes in shared memory (TMA)
+    alignas(64) unsigned char tmap[sgn::kTensorMapBytes] = {};
+    bool tmap_ok = false;                 // tmap describes the bound workspace's texel planes
 };
 
 struct sgn_batch {
@@ -222,6 +225,7 @@ PlanParams make_params(const sgn_plan* p) {
     pp.status = reinterpret_cast<uint8_t*>(b + L.status);
     pp.depth = reinterpret_cast<float*>(b + L.depth);
     pp.sidx = reinterpret_cast<int32_t*>(b + L.sidx);
+    pp.stage_err = sgn::stage_error_word();
     for (int f = 0; f < p->F; ++f) {
         for (int i = 0; i < 3; ++i) {
             for (int j = 0; j < 3; ++j) {
@@ -358,6 +362,22 @@ sgn_status sgn_plan_set_mapping(sgn_plan* p, int lanes_per_surfel, int block_thr
     return SGN_OK;
 }
 
+sgn_status sgn_plan_set_staging(sgn_plan* p, int enabled) {
+    if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "plan is NULL");
+    if (enabled != 0 && enabled != 1) return fail(SGN_ERR_INVALID_ARGUMENT, "enabled must be 0 or 1");
+    p->staging = enabled != 0;
+    return SGN_OK;
+}
+
+sgn_status sgn_staging_timeouts(uint32_t* count) {
+    if (!count) return fail(SGN_ERR_INVALID_ARGUMENT, "count is NULL");
+    unsigned int* w = sgn::stage_error_word();
+    if (!w) return fail(SGN_ERR_CUDA, "staging error counter unavailable");
+    const cudaError_t e = cudaMemcpy(count, w, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the staging timeout counter");
+    return SGN_OK;
+}
+
 sgn_status sgn_plan_bind(sgn_plan* p, void* ws, size_t bytes, void* stream) {
     if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "plan is NULL");
     if (!ws) return fail(SGN_ERR_INVALID_ARGUMENT, "workspace is NULL");
@@ -384,6 +404,7 @@ sgn_status sgn_plan_bind(sgn_plan* p, void* ws, size_t bytes, void* stream) {
     }
     p->ws = static_cast<char*>(ws);
     p->ws_bytes = bytes;
+    p->tmap_ok = false;
     p->stream = static_cast<cudaStream_t>(stream);
     p->device = dev;
     p->kf_set = false;
@@ -566,7 +587,13 @@ static sgn_status run_mode(sgn_plan* p, int iters, int mode) {
     DeviceGuard g(p->device);
     if (mode == sgn::kModeRun && (st = ensure_state(p)) != SGN_OK) return st;
     PlanParams pp = make_params(p);
-    int e = sgn::launch_gn(pp, iters, mode, p->lanes, p->block, p->stream);
+    if (p->staging && !p->tmap_ok) {
+        if (!pp.stage_err) return fail(SGN_ERR_CUDA, "staging error counter unavailable");
+        const int te = sgn::encode_texel_map(p->tmap, pp, p->desc.max_frames);
+        if (te) return cuda_fail(te, "encoding the texel TMA descriptor");
+        p->tmap_ok = true;
+    }
+    int e = sgn::launch_gn(pp, iters, mode, p->lanes, p->block, p->stream, p->staging ? p->tmap : nullptr);
     if (e) return cuda_fail(e, "Gauss-Newton launch");
     sgn::count_launch();
     p->state_pending = false;  // a solve writes the whole working state

@@ -2,6 +2,8 @@
 // texel dtype by gn_f32.cu / gn_f16.cu / gn_bf16.cu.
 #pragma once
 
+#include <cstring>
+
 #include "gn_impl.cuh"
 
 namespace sgn {
@@ -30,17 +32,64 @@ __global__ void __launch_bounds__(256, gn_min_blocks(P, G)) k_gn(const __grid_co
     gn_surfel<P, G, DT>(&spp, gtid / G, threadIdx.x % G, iters, mode, sref[threadIdx.x / G]);
 }
 
+// Staged variant: every group of G lanes owns kStageSlots texel boxes in dynamic shared memory
+// (box_stride(P, DT) bytes each, 128-byte aligned) and one mbarrier per box.
+template <int P, int G, int DT>
+__global__ void __launch_bounds__(256, gn_min_blocks(P, G))
+    k_gn_staged(const __grid_constant__ PlanParams pp, int iters, int mode, const __grid_constant__ TexMap tmap) {
+    __shared__ PlanParams spp;
+    __shared__ float sref[256 / G][kRefStride];
+    __shared__ unsigned long long sbar[256 / G][kStageSlots];
+    extern __shared__ unsigned char sdyn[];
+    const int grp = threadIdx.x / G, lg = threadIdx.x % G;
+    load_plan(&spp, &pp);
+    if (lg == 0)
+        for (int k = 0; k < kStageSlots; ++k) mbar_init(smem_addr(&sbar[grp][k]), 1);
+    fence_mbar_init();
+    __syncthreads();
+    const unsigned base = (smem_addr(sdyn) + 127u) & ~127u;
+    constexpr unsigned group_bytes = kStageSlots * box_stride(P, DT);
+    Stage st;
+    st.tmap = &tmap;
+    st.slots = base + grp * group_bytes;
+    st.bars = smem_addr(&sbar[grp][0]);
+    st.slots_ptr = sdyn + (base - smem_addr(sdyn)) + grp * group_bytes;
+    st.issued = st.consumed = 0;
+    st.broken = false;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    gn_surfel<P, G, DT, true>(&spp, gtid / G, lg, iters, mode, sref[grp], &st);
+}
+
+template <int P, int G, int DT>
+int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st, const void* tmap) {
+    if (!tmap) {
+        k_gn<P, G, DT><<<grid, block, 0, st>>>(pp, iters, mode);
+        return int(cudaGetLastError());
+    }
+    // boxes of the block's groups, plus slack to align them to 128 bytes
+    const int smem = (block / G) * kStageSlots * box_stride(P, DT) + 128;
+    static bool attr_set = false;  // same value from every thread: a benign race
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(k_gn_staged<P, G, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (256 / G) * kStageSlots * box_stride(P, DT) + 128);
+        if (e != cudaSuccess) return int(e);
+        attr_set = true;
+    }
+    TexMap m;
+    memcpy(&m, tmap, sizeof m);
+    k_gn_staged<P, G, DT><<<grid, block, smem, st>>>(pp, iters, mode, m);
+    return int(cudaGetLastError());
+}
+
 template <int DT>
-int launch_gn_dtype(const PlanParams& pp, int iters, int mode, int G, int block, void* stream) {
+int launch_gn_dtype(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap) {
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long threads = (long long)pp.S * G;
     const int grid = int((threads + block - 1) / block);
     if (grid == 0) return cudaSuccess;
-#define SGN_GN_CASE(PP, GG)                                                          \
-    if (pp.P == PP && G == GG) {                                                    \
-        k_gn<PP, GG, DT><<<grid, block, 0, st>>>(pp, iters, mode);                   \
-        return int(cudaGetLastError());                                             \
-    }
+    if (block > 256 || block % G) return int(cudaErrorInvalidConfiguration);
+#define SGN_GN_CASE(PP, GG) \
+    if (pp.P == PP && G == GG) return launch_one<PP, GG, DT>(pp, iters, mode, grid, block, st, tmap);
     SGN_GN_CASE(4, 8)
     SGN_GN_CASE(4, 16)
     SGN_GN_CASE(8, 8)

@@ -2,23 +2,76 @@
 // dtype dispatch of the Gauss-Newton launcher.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "sgn_internal.h"
 
 namespace sgn {
 
-int launch_gn_f32(const PlanParams& pp, int iters, int mode, int G, int block, void* stream);
-int launch_gn_f16(const PlanParams& pp, int iters, int mode, int G, int block, void* stream);
-int launch_gn_bf16(const PlanParams& pp, int iters, int mode, int G, int block, void* stream);
+int launch_gn_f32(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap);
+int launch_gn_f16(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap);
+int launch_gn_bf16(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap);
 
-int launch_gn(const PlanParams& pp, int iters, int mode, int lanes_per_surfel, int block_threads, void* stream) {
+int launch_gn(const PlanParams& pp, int iters, int mode, int lanes_per_surfel, int block_threads, void* stream,
+              const void* tmap) {
     switch (pp.dtype) {
-        case SGN_F32: return launch_gn_f32(pp, iters, mode, lanes_per_surfel, block_threads, stream);
-        case SGN_F16: return launch_gn_f16(pp, iters, mode, lanes_per_surfel, block_threads, stream);
-        case SGN_BF16: return launch_gn_bf16(pp, iters, mode, lanes_per_surfel, block_threads, stream);
+        case SGN_F32: return launch_gn_f32(pp, iters, mode, lanes_per_surfel, block_threads, stream, tmap);
+        case SGN_F16: return launch_gn_f16(pp, iters, mode, lanes_per_surfel, block_threads, stream, tmap);
+        case SGN_BF16: return launch_gn_bf16(pp, iters, mode, lanes_per_surfel, block_threads, stream, tmap);
         default: return int(cudaErrorInvalidValue);
     }
+}
+
+// ------------------------------------------------------------------------------ staging support
+
+namespace {
+__device__ unsigned int g_stage_err;  // staging waits that timed out, all plans of this process
+constexpr int kMaxDevices = 64;
+unsigned int* g_stage_err_addr[kMaxDevices] = {};
+std::mutex g_stage_mutex;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+}  // namespace
+
+unsigned int* stage_error_word() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_stage_mutex);
+    if (!g_stage_err_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_stage_err) != cudaSuccess) return nullptr;
+        g_stage_err_addr[dev] = static_cast<unsigned int*>(p);
+    }
+    return g_stage_err_addr[dev];
+}
+
+// The texel planes as a 3-D tensor of 32-bit (FP32 texels) or 16-bit (FP16/BF16 texels) elements,
+// 4 per texel: (4 W, H, planes) with byte strides (4 tex_pitch e, tex_plane 4 e); box
+// (4 box_w, box_h, 1).  Boxes reaching outside the image are filled with zeros.
+int encode_texel_map(void* tmap, const PlanParams& pp, int planes) {
+    {
+        std::lock_guard<std::mutex> lock(g_stage_mutex);
+        if (!g_encode) {
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q{};
+            const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+            if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return int(e != cudaSuccess ? e : cudaErrorNotSupported);
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        }
+    }
+    const bool f32 = pp.dtype == SGN_F32;
+    const cuuint64_t esize = f32 ? 4 : 2;
+    const cuuint64_t dims[3] = {cuuint64_t(4) * pp.W, cuuint64_t(pp.H), cuuint64_t(planes)};
+    const cuuint64_t strides[2] = {cuuint64_t(pp.tex_pitch) * 4 * esize, cuuint64_t(pp.tex_plane) * 4 * esize};
+    const cuuint32_t box[3] = {cuuint32_t(4 * box_w(pp.P, pp.dtype)), cuuint32_t(box_h(pp.P)), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = g_encode(static_cast<CUtensorMap*>(tmap), f32 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                                3, const_cast<void*>(pp.tex), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? int(cudaSuccess) : int(cudaErrorInvalidValue);
 }
 
 // ------------------------------------------------------------------------------ frame preparation

@@ -59,8 +59,35 @@ struct PlanParams {
     uint8_t* status;
     float* depth;               // W x H, tightly packed
     int32_t* sidx;
+    unsigned int* stage_err;    // device counter of staging waits that timed out (library-wide)
     FramePose frames[kMaxFrames];
 };
+
+// ---- shared-memory staging of frame texels
+// Each (surfel, frame) stages a box of texels around the tile centre's reference projection
+// U_ref = (X_int + X_frac, Y_int + Y_frac): rows Y_int - R .. Y_int + R + 1 and columns from
+// X_int - R (rounded down to even for 8-byte texels, so that a TMA row starts on 16 bytes) over
+// box_w texels.  R = P / 2 + 1 leaves a margin of at least one pixel around the footprint of a P x P
+// tile at unit scale; samples outside the box read global memory.
+#if defined(__CUDACC__)
+#define SGN_HD __host__ __device__
+#else
+#define SGN_HD
+#endif
+SGN_HD constexpr int box_radius(int P) { return P / 2 + 1; }
+SGN_HD constexpr int box_h(int P) { return 2 * box_radius(P) + 2; }
+SGN_HD constexpr int box_w(int P, int dtype) { return dtype == SGN_F32 ? 2 * box_radius(P) + 2 : 2 * box_radius(P) + 4; }
+SGN_HD constexpr int box_bytes(int P, int dtype) { return box_w(P, dtype) * box_h(P) * (dtype == SGN_F32 ? 16 : 8); }
+SGN_HD constexpr int box_stride(int P, int dtype) { return (box_bytes(P, dtype) + 127) / 128 * 128; }
+constexpr int kStageSlots = 2;  // boxes in flight per surfel (double buffering)
+constexpr int kTensorMapBytes = 128;
+
+// Encodes the TMA descriptor of a plan's texel planes (planes frames of H rows, 4 components per
+// texel) with the staging box of patch P into tmap (kTensorMapBytes, 64-byte aligned host memory).
+// Returns cudaError_t cast to int.
+int encode_texel_map(void* tmap, const PlanParams& pp, int planes);
+// Device address of the library-wide staging timeout counter on the current device (nullptr on error).
+unsigned int* stage_error_word();
 
 // Texel element sizes per dtype.
 inline int texel_bytes(int dtype) { return dtype == SGN_F32 ? 16 : 8; }
@@ -74,7 +101,9 @@ enum GnMode : int {
 // Launchers (defined in the .cu files). All return cudaError_t cast to int.
 int launch_prep_frames(const PlanParams& pp, const float* const* src, const size_t* src_pitch_floats, int first,
                        int count, void* stream);
-int launch_gn(const PlanParams& pp, int iters, int mode, int lanes_per_surfel, int block_threads, void* stream);
+// tmap: host copy of the texel TMA descriptor (encode_texel_map), or nullptr for direct gathers.
+int launch_gn(const PlanParams& pp, int iters, int mode, int lanes_per_surfel, int block_threads, void* stream,
+              const void* tmap = nullptr);
 int launch_seed(const PlanParams& pp, void* stream);
 int launch_init_state(const PlanParams& pp, void* stream);
 int launch_render_depth(const PlanParams& pp, void* stream);
