@@ -170,6 +170,7 @@ struct sgn_batch {
     cudaGraphExec_t exec = nullptr;
     int graph_iters = -1;
     int graph_grid = 0;
+    int graph_frames = 0;  // largest frame count the captured launch sizes its scratch for
     cudaEvent_t done = nullptr;
     std::vector<cudaEvent_t> plan_events;
 };
@@ -832,6 +833,7 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
             return ca > cc;
         });
         b->n_items = int(b->h_items.size());
+        batch_drop_graph(b);  // the captured launch holds the item count
         e = cudaMemcpyAsync(b->ws + off_items, b->h_items.data(), b->h_items.size() * sizeof(WorkItem),
                             cudaMemcpyHostToDevice, b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "work list upload");
@@ -841,11 +843,13 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
     if (e != cudaSuccess) return cuda_fail(e, "plan table upload");
     // The persistent launch (counter reset + kernel) is captured once per iteration count and
     // replayed as a CUDA graph.
-    if (!b->exec || b->graph_iters != iters) {
+    int fmax = 1;
+    for (const PlanParams& pp : b->h_plans) fmax = std::max(fmax, pp.F);
+    if (!b->exec || b->graph_iters != iters || b->graph_frames != fmax) {
         batch_drop_graph(b);
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-        const int per_sm = sgn::batch_blocks_per_sm(b->variant, 256);
+        const int per_sm = sgn::batch_blocks_per_sm(b->variant, 256, fmax);
         if (per_sm <= 0) return fail(SGN_ERR_CUDA, "batch kernel cannot be resident");
         b->graph_grid = sms * per_sm;
         cudaStream_t cap = b->stream;
@@ -861,7 +865,7 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
         }
         int le = sgn::launch_gn_batch(reinterpret_cast<const PlanParams*>(b->ws), reinterpret_cast<const WorkItem*>(b->ws + off_items),
                                       b->n_items, reinterpret_cast<int*>(b->ws + off_counter), iters, b->variant,
-                                      b->graph_grid, 256, cap);
+                                      b->graph_grid, 256, fmax, cap);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cap, &graph);
         if (own) cudaStreamDestroy(cap);
@@ -876,6 +880,7 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
             return cuda_fail(e, "cudaGraphInstantiate");
         }
         b->graph_iters = iters;
+        b->graph_frames = fmax;
     }
     if ((e = cudaGraphLaunch(b->exec, b->stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     sgn::count_launch();

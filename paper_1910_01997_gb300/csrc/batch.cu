@@ -20,35 +20,42 @@ int lanes_for_patch(int variant, int P) { return batch_lanes(variant, P); }
 
 template <int P, int G, int DT>
 __device__ __forceinline__ void run_chunk(const PlanParams* pp, int first, int count, int lane, int iters,
-                                          float* ref) {
+                                          float* ref, int group_words) {
     constexpr int SPW = 32 / G;  // surfels per warp step
     const int end = first + count;
     for (int base = first; base < end; base += SPW) {
         const int s = base + lane / G;
-        gn_surfel<P, G, DT>(pp, s < end ? s : pp->S, lane % G, iters, kModeSolve,
-                            ref + (lane / G) * kMaxFrames * kRefWords);
+        gn_surfel<P, G, DT>(pp, s < end ? s : pp->S, lane % G, iters, kModeSolve, ref + (lane / G) * group_words);
         __syncwarp();
     }
 }
 
 template <int V, int DT>
 __device__ __forceinline__ void dispatch_patch(const PlanParams* pp, const WorkItem& w, int lane, int iters,
-                                               float* ref) {
+                                               float* ref, int group_words) {
     switch (pp->P) {
-        case 4: run_chunk<4, batch_lanes(V, 4), DT>(pp, w.first, w.count, lane, iters, ref); break;
-        case 8: run_chunk<8, batch_lanes(V, 8), DT>(pp, w.first, w.count, lane, iters, ref); break;
-        case 16: run_chunk<16, batch_lanes(V, 16), DT>(pp, w.first, w.count, lane, iters, ref); break;
+        case 4: run_chunk<4, batch_lanes(V, 4), DT>(pp, w.first, w.count, lane, iters, ref, group_words); break;
+        case 8: run_chunk<8, batch_lanes(V, 8), DT>(pp, w.first, w.count, lane, iters, ref, group_words); break;
+        case 16: run_chunk<16, batch_lanes(V, 16), DT>(pp, w.first, w.count, lane, iters, ref, group_words); break;
         default: break;
     }
 }
 
+// Groups per warp at most (8 lanes per surfel: 4x4 tiles in variant 0).
+constexpr int kBatchGroups = 4;
+
+// Dynamic shared memory: per warp, kBatchGroups frame scratches of max_frames frames.
+int batch_scratch_bytes(int max_frames) { return kBatchWarps * kBatchGroups * group_scratch_words(max_frames) * 4; }
+
 template <int V>
 __global__ void __launch_bounds__(kBatchBlock, 2) k_gn_batch(const PlanParams* __restrict__ plans,
                                                           const WorkItem* __restrict__ items, int n_items,
-                                                          int* __restrict__ counter, int iters) {
+                                                          int* __restrict__ counter, int iters, int max_frames) {
     __shared__ PlanParams spp[kBatchWarps];
-    __shared__ float sref[kBatchWarps][4 * kMaxFrames * kRefWords];  // up to 4 groups per warp
+    extern __shared__ float4 sdyn[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int group_words = group_scratch_words(max_frames);
+    float* wref = reinterpret_cast<float*>(sdyn) + warp * kBatchGroups * group_words;
     PlanParams* my = &spp[warp];
     int cur = -1;
     for (;;) {
@@ -66,31 +73,46 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_gn_batch(const PlanParams* _
             cur = w.plan;
         }
         switch (my->dtype) {
-            case SGN_F32: dispatch_patch<V, SGN_F32>(my, w, lane, iters, sref[warp]); break;
-            case SGN_F16: dispatch_patch<V, SGN_F16>(my, w, lane, iters, sref[warp]); break;
-            case SGN_BF16: dispatch_patch<V, SGN_BF16>(my, w, lane, iters, sref[warp]); break;
+            case SGN_F32: dispatch_patch<V, SGN_F32>(my, w, lane, iters, wref, group_words); break;
+            case SGN_F16: dispatch_patch<V, SGN_F16>(my, w, lane, iters, wref, group_words); break;
+            case SGN_BF16: dispatch_patch<V, SGN_BF16>(my, w, lane, iters, wref, group_words); break;
             default: break;
         }
     }
 }
 
-int batch_blocks_per_sm(int variant, int block_threads) {
+static cudaError_t batch_attributes() {
+    static bool done = false;  // same values from every thread: a benign race
+    if (done) return cudaSuccess;
+    const int max_bytes = batch_scratch_bytes(kMaxFrames);
+    cudaError_t e = cudaFuncSetAttribute(k_gn_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gn_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+int batch_blocks_per_sm(int variant, int block_threads, int max_frames) {
+    if (batch_attributes() != cudaSuccess) return 0;
     int n = 0;
-    cudaError_t e = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gn_batch<0>, block_threads, 0)
-                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gn_batch<1>, block_threads, 0);
+    const size_t smem = batch_scratch_bytes(max_frames);
+    cudaError_t e = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gn_batch<0>, block_threads, smem)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gn_batch<1>, block_threads, smem);
     return e == cudaSuccess ? n : 0;
 }
 
 int launch_gn_batch(const PlanParams* d_plans, const WorkItem* d_items, int n_items, int* d_counter, int iters,
-                    int variant, int grid, int block_threads, void* stream) {
+                    int variant, int grid, int block_threads, int max_frames, void* stream) {
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (block_threads != kBatchBlock) return int(cudaErrorInvalidConfiguration);
-    cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+    if (block_threads != kBatchBlock || max_frames < 1 || max_frames > kMaxFrames) return int(cudaErrorInvalidConfiguration);
+    cudaError_t e = batch_attributes();
     if (e != cudaSuccess) return int(e);
+    e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return int(e);
+    const size_t smem = batch_scratch_bytes(max_frames);
     if (variant == 0)
-        k_gn_batch<0><<<grid, block_threads, 0, st>>>(d_plans, d_items, n_items, d_counter, iters);
+        k_gn_batch<0><<<grid, block_threads, smem, st>>>(d_plans, d_items, n_items, d_counter, iters, max_frames);
     else
-        k_gn_batch<1><<<grid, block_threads, 0, st>>>(d_plans, d_items, n_items, d_counter, iters);
+        k_gn_batch<1><<<grid, block_threads, smem, st>>>(d_plans, d_items, n_items, d_counter, iters, max_frames);
     return int(cudaGetLastError());
 }
 

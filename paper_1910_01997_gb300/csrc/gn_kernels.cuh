@@ -20,58 +20,71 @@ __device__ __forceinline__ void load_plan(PlanParams* dst, const PlanParams* src
 // per lane: with 4800 surfels of 8x8 pixels (a 640x480 keyframe) at 16 or 8 lanes per surfel every
 // surfel is resident in a single wave on 152 SMs.
 constexpr int gn_min_blocks(int P, int G) { return P * P / G <= 2 ? 3 : (P * P / G == 4 ? 2 : 1); }
-constexpr int kRefStride = kMaxFrames * kRefWords + 1;  // odd stride: groups of a warp use distinct banks
+
+// Dynamic shared memory of a launch: each group's frame scratch (group_scratch_words(F) floats,
+// 16-byte aligned), then, when staging, each group's texel boxes (128-byte aligned).
+__host__ __device__ constexpr int scratch_bytes(int groups, int F) { return groups * group_scratch_words(F) * 4; }
 
 template <int P, int G, int DT>
 __global__ void __launch_bounds__(256, gn_min_blocks(P, G)) k_gn(const __grid_constant__ PlanParams pp, int iters, int mode) {
     __shared__ PlanParams spp;
-    __shared__ float sref[256 / G][kRefStride];
+    extern __shared__ float4 sdyn[];
     load_plan(&spp, &pp);
     __syncthreads();
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    gn_surfel<P, G, DT>(&spp, gtid / G, threadIdx.x % G, iters, mode, sref[threadIdx.x / G]);
+    float* scratch = reinterpret_cast<float*>(sdyn) + (threadIdx.x / G) * group_scratch_words(pp.F);
+    gn_surfel<P, G, DT>(&spp, gtid / G, threadIdx.x % G, iters, mode, scratch);
 }
 
-// Staged variant: every group of G lanes owns kStageSlots texel boxes in dynamic shared memory
-// (box_stride(P, DT) bytes each, 128-byte aligned) and one mbarrier per box.
+// Staged variant: every group of G lanes also owns kStageSlots texel boxes (box_stride(P, DT) bytes
+// each) and one mbarrier per box.
 template <int P, int G, int DT>
 __global__ void __launch_bounds__(256, gn_min_blocks(P, G))
     k_gn_staged(const __grid_constant__ PlanParams pp, int iters, int mode, const __grid_constant__ TexMap tmap) {
     __shared__ PlanParams spp;
-    __shared__ float sref[256 / G][kRefStride];
     __shared__ unsigned long long sbar[256 / G][kStageSlots];
-    extern __shared__ unsigned char sdyn[];
+    extern __shared__ float4 sdyn[];
     const int grp = threadIdx.x / G, lg = threadIdx.x % G;
     load_plan(&spp, &pp);
     if (lg == 0)
         for (int k = 0; k < kStageSlots; ++k) mbar_init(smem_addr(&sbar[grp][k]), 1);
     fence_mbar_init();
     __syncthreads();
-    const unsigned base = (smem_addr(sdyn) + 127u) & ~127u;
+    unsigned char* dyn = reinterpret_cast<unsigned char*>(sdyn);
+    const unsigned boxes0 = (smem_addr(dyn) + scratch_bytes(blockDim.x / G, pp.F) + 127u) & ~127u;
     constexpr unsigned group_bytes = kStageSlots * box_stride(P, DT);
     Stage st;
     st.tmap = &tmap;
-    st.slots = base + grp * group_bytes;
+    st.slots = boxes0 + grp * group_bytes;
     st.bars = smem_addr(&sbar[grp][0]);
-    st.slots_ptr = sdyn + (base - smem_addr(sdyn)) + grp * group_bytes;
+    st.slots_ptr = dyn + (st.slots - smem_addr(dyn));
     st.issued = st.consumed = 0;
     st.broken = false;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    gn_surfel<P, G, DT, true>(&spp, gtid / G, lg, iters, mode, sref[grp], &st);
+    float* scratch = reinterpret_cast<float*>(sdyn) + grp * group_scratch_words(pp.F);
+    gn_surfel<P, G, DT, true>(&spp, gtid / G, lg, iters, mode, scratch, &st);
 }
 
 template <int P, int G, int DT>
 int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st, const void* tmap) {
+    const int scratch = scratch_bytes(block / G, pp.F);
     if (!tmap) {
-        k_gn<P, G, DT><<<grid, block, 0, st>>>(pp, iters, mode);
+        static bool attr_set = false;  // same value from every thread: a benign race
+        if (!attr_set) {
+            const cudaError_t e = cudaFuncSetAttribute(k_gn<P, G, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       scratch_bytes(256 / G, kMaxFrames));
+            if (e != cudaSuccess) return int(e);
+            attr_set = true;
+        }
+        k_gn<P, G, DT><<<grid, block, scratch, st>>>(pp, iters, mode);
         return int(cudaGetLastError());
     }
-    // boxes of the block's groups, plus slack to align them to 128 bytes
-    const int smem = (block / G) * kStageSlots * box_stride(P, DT) + 128;
-    static bool attr_set = false;  // same value from every thread: a benign race
+    // boxes of the block's groups after the scratch, plus slack to align them to 128 bytes
+    const int smem = scratch + (block / G) * kStageSlots * box_stride(P, DT) + 128;
+    static bool attr_set = false;
     if (!attr_set) {
         const cudaError_t e = cudaFuncSetAttribute(k_gn_staged<P, G, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (256 / G) * kStageSlots * box_stride(P, DT) + 128);
+                                                   scratch_bytes(256 / G, kMaxFrames) + (256 / G) * kStageSlots * box_stride(P, DT) + 128);
         if (e != cudaSuccess) return int(e);
         attr_set = true;
     }

@@ -122,7 +122,7 @@ struct sgn_server {
     char* tables[2] = {nullptr, nullptr};
     size_t table_bytes = 0;
     int max_items = 0;
-    int grid = 0;
+    int sms = 0;  // multiprocessors of the device (the launch grid is sms x resident blocks)
     bool table_busy[2] = {false, false};
     std::vector<sgn::PlanParams> h_plans;
     std::vector<sgn::WorkItem> h_items;
@@ -244,9 +244,12 @@ sgn_status launch_epoch(sgn_server* s, std::vector<Job*>& jobs, Epoch* ep) {
         cudaMemcpyAsync(items, s->h_items.data(), s->h_items.size() * sizeof(sgn::WorkItem), cudaMemcpyHostToDevice,
                         s->compute) != cudaSuccess)
         return srv_error(SGN_ERR_CUDA, "server: table upload");
+    int fmax = 1;
+    for (const sgn::PlanParams& pp : s->h_plans) fmax = std::max(fmax, pp.F);
+    const int grid = s->sms * std::max(1, sgn::batch_blocks_per_sm(0, 256, fmax));
     int le = sgn::launch_gn_batch(reinterpret_cast<const sgn::PlanParams*>(base),
                                   reinterpret_cast<const sgn::WorkItem*>(items), int(s->h_items.size()), counter,
-                                  jobs[0]->req.iters, 0, s->grid, 256, s->compute);
+                                  jobs[0]->req.iters, 0, grid, 256, fmax, s->compute);
     if (le) return srv_error(SGN_ERR_CUDA, std::string("server: batch launch: ") + cudaGetErrorString(cudaError_t(le)));
     sgn::count_launch();
     if (cudaEventCreateWithFlags(&ep->done, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(ep->done, s->compute) != cudaSuccess)
@@ -426,9 +429,7 @@ sgn_status sgn_server_create(void* d_arena, size_t arena_bytes, int max_slots, i
         delete s;
         return srv_error(SGN_ERR_CUDA, "server: cudaGetDevice");
     }
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    s->grid = sms * std::max(1, sgn::batch_blocks_per_sm(0, 256));
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     s->worker = std::thread(server_loop, s);
     *out = s;
     return SGN_OK;

@@ -6,6 +6,12 @@
 
 #include "sgn.h"
 
+#if defined(__CUDACC__)
+#define SGN_HD __host__ __device__
+#else
+#define SGN_HD
+#endif
+
 namespace sgn {
 
 constexpr int kMaxFrames = SGN_MAX_FRAMES;
@@ -25,6 +31,14 @@ struct FramePose {
 // arithmetic, U_ref = (X_int + X_frac, Y_int + Y_frac), with the centre point q_ref = R r_s + t id_ref,
 // 1 / q_ref_z and e = (fx (t_x q_z - q_x t_z), fy (t_y q_z - q_y t_z)) for the per-iteration update.
 constexpr int kRefWords = 10;
+// Per surfel and frame, the Gauss-Newton kernels keep in shared memory the kRefWords reference words
+// (padded to 12) and the frame's local projective map of the current pass (24 words, 16-byte
+// aligned): kFrameWords floats per frame.  A group's scratch holds F frames plus 4 words of padding,
+// so that the groups of a warp read different shared-memory banks.
+constexpr int kMapOffset = 12;
+constexpr int kMapWords = 24;
+constexpr int kFrameWords = kMapOffset + kMapWords;
+SGN_HD constexpr int group_scratch_words(int F) { return F * kFrameWords + 4; }
 
 // Everything a kernel needs to solve the surfels of one keyframe problem.
 // Lives in kernel parameters (plain launch) or in a device table (batched launch); kernels
@@ -69,11 +83,6 @@ struct PlanParams {
 // X_int - R (rounded down to even for 8-byte texels, so that a TMA row starts on 16 bytes) over
 // box_w texels.  R = P / 2 + 1 leaves a margin of at least one pixel around the footprint of a P x P
 // tile at unit scale; samples outside the box read global memory.
-#if defined(__CUDACC__)
-#define SGN_HD __host__ __device__
-#else
-#define SGN_HD
-#endif
 SGN_HD constexpr int box_radius(int P) { return P / 2 + 1; }
 SGN_HD constexpr int box_h(int P) { return 2 * box_radius(P) + 2; }
 SGN_HD constexpr int box_w(int P, int dtype) { return dtype == SGN_F32 ? 2 * box_radius(P) + 2 : 2 * box_radius(P) + 4; }
@@ -116,9 +125,10 @@ struct WorkItem {
     int pad;
 };
 // variant 0: lanes per surfel P4->8, P8->16, P16->32; variant 1: P4->16, P8->32, P16->32.
+// max_frames: the largest frame count of the batch's plans (sizes the shared-memory scratch).
 int launch_gn_batch(const PlanParams* d_plans, const WorkItem* d_items, int n_items, int* d_counter, int iters,
-                    int variant, int grid, int block_threads, void* stream);
-int batch_blocks_per_sm(int variant, int block_threads);
+                    int variant, int grid, int block_threads, int max_frames, void* stream);
+int batch_blocks_per_sm(int variant, int block_threads, int max_frames);
 int lanes_for_patch(int variant, int P);
 
 void count_launch(uint64_t n = 1);
