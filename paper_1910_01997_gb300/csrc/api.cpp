@@ -825,9 +825,12 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
             for (int f = 0; f < p->S; f += b->chunk)
                 b->h_items.push_back(WorkItem{int(i), f, std::min(b->chunk, p->S - f), 0});
         }
+        // Items of one patch size run the same code path: grouping them (largest patch first) keeps
+        // the warps of an SM on one solver variant at a time; within a group, largest cost first.
         std::stable_sort(b->h_items.begin(), b->h_items.end(), [&](const WorkItem& a, const WorkItem& c) {
             const sgn_plan* pa = b->plans[a.plan];
             const sgn_plan* pc = b->plans[c.plan];
+            if (pa->desc.patch != pc->desc.patch) return pa->desc.patch > pc->desc.patch;
             const double ca = double(a.count) * pa->desc.patch * pa->desc.patch * std::max(1, pa->F);
             const double cc = double(c.count) * pc->desc.patch * pc->desc.patch * std::max(1, pc->F);
             return ca > cc;

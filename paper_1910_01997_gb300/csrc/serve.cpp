@@ -232,6 +232,7 @@ sgn_status launch_epoch(sgn_server* s, std::vector<Job*>& jobs, Epoch* ep) {
     std::stable_sort(s->h_items.begin(), s->h_items.end(), [&](const sgn::WorkItem& a, const sgn::WorkItem& b) {
         const sgn::PlanParams& pa = s->h_plans[a.plan];
         const sgn::PlanParams& pb = s->h_plans[b.plan];
+        if (pa.P != pb.P) return pa.P > pb.P;  // one solver variant at a time (see the batch work list)
         return double(a.count) * pa.P * pa.P * pa.F > double(b.count) * pb.P * pb.P * pb.F;
     });
     if (int(s->h_items.size()) > s->max_items) return srv_error(SGN_ERR_ADMISSION, "server: work list overflow");
