@@ -211,6 +211,54 @@ def batch_leg(dtype: str, stream, dev, reps: int = 5):
             "unit": "residuals/s"}
 
 
+def ablation_leg(prob, stream, reps: int = 20):
+    """Depth-only ablation (Sec. 4.4) on the benchmark workload: the same solve with the normal
+    optimised and with d id_u / d n = 0, each scored against the scene's ground truth (per-pixel
+    inverse depth of the returned map, per-surfel normal angle) and timed (Gauss-Newton launch)."""
+    import numpy as np
+    import torch
+
+    import paper_1910_01997_gb300 as sgn
+
+    _, pid, dep = prob.scene.render(0)  # noise-free keyframe: primitive ids and z-depth per pixel
+    iters = WORKLOAD["iterations"]
+    res = {}
+    with torch.cuda.stream(stream):
+        for name, opt_n in (("full", True), ("depth_only", False)):
+            plan = sgn.Plan(prob.W, prob.H, prob.P, prob.F, WORKLOAD["texels"], stream=stream, optimize_normal=opt_n)
+            plan.set_intrinsics(*prob.cam)
+            plan.set_keyframe(prob.keyframe)
+            plan.set_frames(prob.frames, prob.poses)
+            plan.init_surfels(prob.id0, prob.n0, prob.state)
+            plan.solve(iters)
+            stream.synchronize()
+            t = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                plan.solve(iters)
+                b.record(stream)
+                b.synchronize()
+                t.append(a.elapsed_time(b))
+            out = plan.read_surfels()
+            inv_depth, sidx = plan.read_depth_map()
+            m = sidx >= 0
+            tp = np.full(sidx.shape, -1)
+            tp[m] = prob.tile_prim[sidx[m]]
+            m &= (tp >= 0) & (pid == tp) & (dep > 0)
+            rel = np.abs(inv_depth[m] * dep[m] - 1.0)
+            ok = ((out["status"] & 0x3F) == 0) & (prob.tile_prim >= 0)
+            cosang = np.abs(np.einsum("ij,ij->i", out["n"][ok], prob.gt_n[ok])) / np.linalg.norm(out["n"][ok], axis=1)
+            ang = np.degrees(np.arccos(np.clip(cosang, 0.0, 1.0)))
+            res[name] = {"depth_rel_median": float(np.median(rel)), "depth_rel_p90": float(np.quantile(rel, 0.9)),
+                         "normal_deg_median": float(np.median(ang)), "pixels": int(m.sum()), "surfels": int(ok.sum()),
+                         "solve_ms": statistics.median(t)}
+            plan.close()
+    res["note"] = ("per-pixel inverse depth of the returned depth map vs the noise-free render; surfels start "
+                   "within 10 % / 10 deg of ground truth; at 2.5 cm baselines the normals are weakly observable")
+    return res
+
+
 def serving_leg(duration_s: float, dev, streams: int = 16, rate_hz: float = 5.0, burst: int = 96):
     """Config-5 leg: 16 simulated camera streams submit keyframe solves (Poisson arrivals, 5/s per
     stream; half 640x480, half 1280x720; 8x8 surfels, 4 frames, FP16 texels, 10 iterations) to the
@@ -490,6 +538,7 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_batch:
         line["batch"] = [batch_leg(dt, stream, dev) for dt in ("f32", "f16")]
+        line["ablation"] = ablation_leg(prob, stream)
     if rank == 0 and args.serve_seconds > 0:
         line["serving"] = serving_leg(args.serve_seconds, dev)
     if rank == 0 and not args.no_cpu_baseline:

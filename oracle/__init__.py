@@ -85,6 +85,8 @@ def _load():
                 "orc_seed": (None, [_V, _D, _D, _V, _D, _D, _V]),
                 "orc_depth_map": (None, [_V, _D, _D, _V, _D, _V]),
                 "orc_cost_grid": (None, [_V, ctypes.POINTER(Params), c_i, ctypes.c_long, _D, _D, _D, _V]),
+                "orc_transfer_surfels": (None, [_D, _D, c_i, _D, _D, _D, _D, _D, _D, _V]),
+                "orc_render_surfels": (None, [_D, c_i, c_i, c_i, _D, _D, _D, _V, c_d, _D, _V, _V]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -108,6 +110,36 @@ def _vec(x, n=3):
 
 
 # ------------------------------------------------------------------------------ per-step functions
+
+
+def transfer_surfels(cam, T, u, inv_depth, normal):
+    """Sec. 2.5, Eq. 10: free surfels (pixel u_s (n, 2), inverse depth (n,), normal (n, 3)) of
+    reference frame kf0 expressed in kf1, T (3, 4) mapping kf0 to kf1 coordinates.  Returns
+    (u, inv_depth, normal, valid)."""
+    cam = np.ascontiguousarray(cam, dtype=np.float64).reshape(4)
+    T = np.ascontiguousarray(T, dtype=np.float64).reshape(12)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 2)
+    idv = np.ascontiguousarray(inv_depth, dtype=np.float64).reshape(-1)
+    nv = np.ascontiguousarray(normal, dtype=np.float64).reshape(-1, 3)
+    n = len(idv)
+    uo, io, no, valid = np.empty((n, 2)), np.empty(n), np.empty((n, 3)), np.empty(n, np.uint8)
+    _load().orc_transfer_surfels(_d(cam), _d(T), n, _d(u), _d(idv), _d(nv), _d(uo), _d(io), _d(no), _v(valid))
+    return uo, io, no, valid
+
+
+def render_surfels(cam, W, H, u, inv_depth, normal, valid, radius, with_second=False):
+    """Sec. 2.2 depth-buffered render of free surfels of radius ``radius`` (Eq. 3, Eq. 4).
+    Returns (inv_depth (H, W), surfel index (H, W)[, runner-up inverse depth (H, W)])."""
+    cam = np.ascontiguousarray(cam, dtype=np.float64).reshape(4)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 2)
+    idv = np.ascontiguousarray(inv_depth, dtype=np.float64).reshape(-1)
+    nv = np.ascontiguousarray(normal, dtype=np.float64).reshape(-1, 3)
+    valid = np.ascontiguousarray(valid, dtype=np.uint8).reshape(-1)
+    inv, sidx = np.empty((H, W)), np.empty((H, W), np.int32)
+    second = np.empty((H, W)) if with_second else None
+    _load().orc_render_surfels(_d(cam), int(W), int(H), len(idv), _d(u), _d(idv), _d(nv), _v(valid), float(radius),
+                               _d(inv), _v(sidx), _v(second))
+    return (inv, sidx, second) if with_second else (inv, sidx)
 
 
 def gradients(img):

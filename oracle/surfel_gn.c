@@ -34,7 +34,11 @@
  *  - Eq. 3 is unchanged when n changes sign, so after each update the normal is
  *    turned to face the camera (n . r_s < 0); this fixes the representation only;
  *  - seeding (Sec. 2.3): one Jacobi pass over tiles marked TO_SEED, using the
- *    8-connected tiles that were VALID before the pass as the neighbours.
+ *    8-connected tiles that were VALID before the pass as the neighbours;
+ *  - reference-frame change (Sec. 2.5, Eq. 10) and the depth-buffered render of
+ *    free surfels (Sec. 2.2, Eq. 3 and Eq. 4): a surfel covers the pixels whose
+ *    centre is within radius r of its projected point; the nearest wins and
+ *    equal inverse depths go to the lower surfel index.
  *
  * Parity pins: every function below is pinned by a test in tests/ against
  * closed forms, finite differences, library routines or brute force; the
@@ -562,5 +566,81 @@ void orc_cost_grid(const void* p, const orc_params* prm, int s, long m, const do
         orc_eval_surfel(p, prm, s, ids[i], normals + 3 * i, H, g, &e, &c, &mg, NULL, NULL);
         E[i] = e;
         cnt[i] = c;
+    }
+}
+
+/*
+ * ---- Reference-frame change and the depth-buffered surfel render (Sec. 2.5, Sec. 2.2) ----
+ *
+ * A free surfel is given by the pixel u_s where its point projects in its reference frame, its
+ * inverse depth id_s along r_s = K^-1 (u_s, 1) (z = 1), and its normal n.
+ */
+
+/*
+ * Sec. 2.5, Eq. 10: move surfels from reference frame kf0 to kf1.  T is the row-major [R | t]
+ * that maps kf0 coordinates to kf1 coordinates.  p0 = r_s / id_s, p1 = R p0 + t, n1 = R n0;
+ * the new ray is pi(p1) = p1 / p1_z, so id1 = 1 / p1_z and u1 = (fx r1_x + cx, fy r1_y + cy).
+ * valid[i] = 0 when id_s <= 0 or the point lands behind the new camera (p1_z <= 0); the
+ * outputs of such a surfel are zero.
+ */
+void orc_transfer_surfels(const double cam[4], const double T[12], int n, const double* u_in, const double* id_in,
+                          const double* n_in, double* u_out, double* id_out, double* n_out, uint8_t* valid) {
+    for (int i = 0; i < n; ++i) {
+        double r0[3], p0[3], p1[3], n1[3];
+        orc_ray(cam[0], cam[1], cam[2], cam[3], u_in[2 * i], u_in[2 * i + 1], r0);
+        const double id0 = id_in[i];
+        for (int k = 0; k < 3; ++k) p0[k] = r0[k] / id0;
+        for (int k = 0; k < 3; ++k) {
+            p1[k] = T[4 * k] * p0[0] + T[4 * k + 1] * p0[1] + T[4 * k + 2] * p0[2] + T[4 * k + 3];
+            n1[k] = T[4 * k] * n_in[3 * i] + T[4 * k + 1] * n_in[3 * i + 1] + T[4 * k + 2] * n_in[3 * i + 2];
+        }
+        const int ok = id0 > 0.0 && isfinite(id0) && p1[2] > 0.0 && isfinite(p1[2]);
+        valid[i] = (uint8_t)ok;
+        u_out[2 * i] = ok ? cam[0] * (p1[0] / p1[2]) + cam[2] : 0.0;
+        u_out[2 * i + 1] = ok ? cam[1] * (p1[1] / p1[2]) + cam[3] : 0.0;
+        id_out[i] = ok ? 1.0 / p1[2] : 0.0;
+        for (int k = 0; k < 3; ++k) n_out[3 * i + k] = ok ? n1[k] : 0.0;
+    }
+}
+
+/*
+ * Sec. 2.2 with the depth buffer: every valid surfel covers the pixels u whose centre lies within
+ * radius r of u_s (Eq. 4, |u_s - u| < r); at a covered pixel its inverse depth is Eq. 3 along the
+ * surfel's own ray, id_u = id_s (r_u . n) / (r_s . n), drawn only when positive and finite.  Where
+ * several surfels cover a pixel the nearest one (largest id_u) is kept, ties going to the lower
+ * surfel index; inv_depth and sidx get 0 and -1 where no surfel is drawn.  second[] (may be NULL)
+ * receives the largest id_u among the other surfels drawn at the pixel (0 if none), for tests
+ * that must tell a unique winner from a near tie.
+ */
+void orc_render_surfels(const double cam[4], int W, int H, int n, const double* u, const double* id, const double* nrm,
+                        const uint8_t* valid, double radius, double* inv_depth, int32_t* sidx, double* second) {
+    for (long k = 0; k < (long)W * H; ++k) {
+        inv_depth[k] = 0.0;
+        sidx[k] = -1;
+        if (second) second[k] = 0.0;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!valid[i]) continue;
+        double r_s[3];
+        orc_ray(cam[0], cam[1], cam[2], cam[3], u[2 * i], u[2 * i + 1], r_s);
+        const int x0 = (int)floor(u[2 * i] - radius), x1 = (int)ceil(u[2 * i] + radius);
+        const int y0 = (int)floor(u[2 * i + 1] - radius), y1 = (int)ceil(u[2 * i + 1] + radius);
+        for (int y = y0 < 0 ? 0 : y0; y <= y1 && y < H; ++y)
+            for (int x = x0 < 0 ? 0 : x0; x <= x1 && x < W; ++x) {
+                const double dx = u[2 * i] - x, dy = u[2 * i + 1] - y;
+                if (!(sqrt(dx * dx + dy * dy) < radius)) continue;
+                double r_u[3];
+                orc_ray(cam[0], cam[1], cam[2], cam[3], x, y, r_u);
+                const double v = orc_inv_depth(r_u, r_s, id[i], nrm + 3 * i);
+                if (!isfinite(v) || !(v > 0.0)) continue;
+                const long k = (long)y * W + x;
+                if (v > inv_depth[k]) {  /* nearer: the current winner becomes the runner-up */
+                    if (second && sidx[k] >= 0) second[k] = inv_depth[k];
+                    inv_depth[k] = v;
+                    sidx[k] = i;
+                } else if (second && v > second[k]) {
+                    second[k] = v;  /* equal or farther: ties keep the lower index */
+                }
+            }
     }
 }

@@ -201,3 +201,20 @@ def compare(prob, g, o, margin_px=1e-3, min_normal_eig=None, stable=None):
             st[name + "ang_med"] = float(np.median(ang[m]))
     st["rel"], st["ang"], st["mask"] = rel, ang, cmp
     return st
+
+
+def gt_errors(prob, out):
+    """Quality of a solve against the scene's ground truth: per-pixel inverse depth of the returned
+    depth map vs the renderer's (noise-free keyframe, pixels of tiles that see one primitive and
+    whose own primitive is that one), and per-surfel normal angle vs the primitive's normal."""
+    _, pid, dep = prob.scene.render(0)
+    sidx = out["sidx"]
+    m = sidx >= 0
+    tp = np.full(sidx.shape, -1)
+    tp[m] = prob.tile_prim[sidx[m]]
+    m &= (tp >= 0) & (pid == tp) & np.isfinite(dep) & (dep > 0)
+    rel = np.abs(out["inv_depth"][m] * dep[m] - 1.0)
+    ok = ((out["status"] & 0x3F) == 0) & (prob.tile_prim >= 0)
+    ang = angle_deg(out["n"][ok], prob.gt_n[ok])
+    return dict(pixels=int(m.sum()), depth_rel_median=float(np.median(rel)), depth_rel_p90=float(np.quantile(rel, 0.9)),
+                surfels=int(ok.sum()), normal_deg_median=float(np.median(ang)), normal_deg_p90=float(np.quantile(ang, 0.9)))

@@ -54,12 +54,33 @@ MUTANTS = {
     "tile centre off by half a pixel": (
         "double ux = tx * pb->P + 0.5 * (pb->P - 1), uy = ty * pb->P + 0.5 * (pb->P - 1);",
         "double ux = tx * pb->P + 0.5 * pb->P, uy = ty * pb->P + 0.5 * pb->P;"),
+    # reference-frame change and depth-buffered render (pinned by test_oracle_transfer.py)
+    "frame change with transposed rotation": (
+        "p1[k] = T[4 * k] * p0[0] + T[4 * k + 1] * p0[1] + T[4 * k + 2] * p0[2] + T[4 * k + 3];",
+        "p1[k] = T[k] * p0[0] + T[4 + k] * p0[1] + T[8 + k] * p0[2] + T[4 * k + 3];", "transfer"),
+    "frame change without translation": (
+        "p1[k] = T[4 * k] * p0[0] + T[4 * k + 1] * p0[1] + T[4 * k + 2] * p0[2] + T[4 * k + 3];",
+        "p1[k] = T[4 * k] * p0[0] + T[4 * k + 1] * p0[1] + T[4 * k + 2] * p0[2];", "transfer"),
+    "frame change leaves the normal unrotated": (
+        "n1[k] = T[4 * k] * n_in[3 * i] + T[4 * k + 1] * n_in[3 * i + 1] + T[4 * k + 2] * n_in[3 * i + 2];",
+        "n1[k] = n_in[3 * i + k];", "transfer"),
+    "new inverse depth taken as the depth": (
+        "id_out[i] = ok ? 1.0 / p1[2] : 0.0;", "id_out[i] = ok ? p1[2] : 0.0;", "transfer"),
+    "render keeps the farthest surfel": (
+        "if (v > inv_depth[k]) {", "if (sidx[k] < 0 || v < inv_depth[k]) {", "transfer"),
+    "render ties go to the higher index": (
+        "if (v > inv_depth[k]) {", "if (v >= inv_depth[k]) {", "transfer"),
+    "render radius test inclusive": (
+        "if (!(sqrt(dx * dx + dy * dy) < radius)) continue;",
+        "if (!(sqrt(dx * dx + dy * dy) <= radius)) continue;", "transfer"),
 }
+PIN_FILES = {None: "test_oracle_pins.py", "transfer": "test_oracle_transfer.py"}
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_reject_planted_mistake(name, tmp_path):
-    old, new = MUTANTS[name]
+    old, new, *which = MUTANTS[name]
+    pins = PIN_FILES[which[0] if which else None]
     src = open(SRC).read()
     assert src.count(old) == 1, name
     mut = tmp_path / "mutant.c"
@@ -69,6 +90,6 @@ def test_pins_reject_planted_mistake(name, tmp_path):
                            str(mut), "-o", str(so), "-lm"])
     env = dict(os.environ, ORACLE_SO=str(so), OMP_NUM_THREADS="4")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
