@@ -284,6 +284,36 @@ sgn_status sgn_server_stats(sgn_server* server, sgn_serving_stats* out);
 /* Finish the requests in flight, then stop the server thread. */
 sgn_status sgn_server_destroy(sgn_server* server);
 
+/* ---- reference-frame change and surfel render (Sec. 2.5, Sec. 2.2) ------------------------ */
+
+/* A free surfel is the pixel u_s = (x, y) where its point projects in its reference frame, its
+ * inverse depth id_s along the ray r_s = K^-1 (u_s, 1) (z = 1), and its unit normal n = (x, y, z).
+ * A plan's surfel s is the free surfel at its tile centre (tx P + (P-1)/2, ty P + (P-1)/2). */
+
+/* Sec. 2.5, Eq. 10: express n free surfels of reference frame kf0 in reference frame kf1.
+ * T_kf1_kf0: host array of 12 doubles, row-major [R | t] mapping kf0 coordinates to kf1
+ * coordinates (a finite rigid motion, else SGN_ERR_INVALID_ARGUMENT).  For each surfel
+ * p1 = R r_s / id_s + t, n1 = R n, u1 = pi(K p1) and id1 = 1 / p1_z; valid[i] = 1, or 0 (all
+ * outputs 0) when id_s <= 0 or p1 lies behind the new camera.  Device arrays: u, u_out 2n floats
+ * (8-byte aligned), inv_depth, inv_depth_out n floats, normal, normal_out 3n floats, valid n
+ * bytes; inputs and outputs must not overlap.  FP32 arithmetic.  Asynchronous on `stream`
+ * (cudaStream_t, may be NULL); n = 0 is a no-op. */
+sgn_status sgn_transfer_surfels(const double intrinsics[4], const double T_kf1_kf0[12], int n, const float* u,
+                                const float* inv_depth, const float* normal, float* u_out, float* inv_depth_out,
+                                float* normal_out, uint8_t* valid, void* stream);
+
+/* Sec. 2.2: depth-buffered render of n free surfels of radius `radius` pixels (0 < radius <= 1024)
+ * into a width x height map.  A surfel covers the pixels whose centre lies strictly within the
+ * radius of u_s (Eq. 4); at a covered pixel its inverse depth is Eq. 3 along its own ray, drawn
+ * when positive.  The nearest surfel (largest inverse depth) is kept; equal inverse depths go to
+ * the lower index.  inv_depth_map (floats) and surfel_index (int32) get 0 and -1 where no surfel
+ * is drawn.  zbuffer: caller scratch of width * height uint64 (device).  Surfels with
+ * valid[i] == 0 are skipped.  Surfel arrays as for sgn_transfer_surfels (device; may be NULL
+ * when n = 0).  FP32 arithmetic; asynchronous on `stream`. */
+sgn_status sgn_render_surfels(const double intrinsics[4], int width, int height, int n, const float* u,
+                              const float* inv_depth, const float* normal, const uint8_t* valid, float radius,
+                              uint64_t* zbuffer, float* inv_depth_map, int32_t* surfel_index, void* stream);
+
 /* ---- autotuning -------------------------------------------------------------------------- */
 
 /* Choose the plan's kernel mapping (lanes per surfel x threads per block, as in

@@ -119,6 +119,9 @@ _SIGS = {
     "sgn_batch_destroy": [_P],
     "sgn_check_fp64_reciprocal": [_P, _P, _I, _P],
     "sgn_plan_set_staging": [_P, _I],
+    "sgn_transfer_surfels": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _I, _P, _P, _P, _P, _P,
+                             _P, _P, _P],
+    "sgn_render_surfels": [ctypes.POINTER(ctypes.c_double), _I, _I, _I, _P, _P, _P, _P, ctypes.c_float, _P, _P, _P, _P],
     "sgn_staging_timeouts": [ctypes.POINTER(ctypes.c_uint32)],
 }
 for _name, _args in _SIGS.items():
@@ -362,6 +365,55 @@ def sgn_launch_count() -> int:
 
 def sgn_abi_version() -> int:
     return int(_lib.sgn_abi_version())
+
+
+def _doubles(values, n):
+    a = (ctypes.c_double * n)(*[float(v) for v in np.asarray(values, dtype=np.float64).reshape(-1)])
+    if len(np.asarray(values).reshape(-1)) != n:
+        raise ValueError(f"expected {n} values")
+    return a
+
+
+def _dev(t, dtype, shape):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+            and tuple(t.shape) == tuple(shape)):
+        raise ValueError(f"expected a contiguous CUDA tensor of {dtype} and shape {tuple(shape)}")
+    return t.data_ptr()
+
+
+def sgn_transfer_surfels(intrinsics, T_kf1_kf0, u, inv_depth, normal, stream=None):
+    """Sec. 2.5, Eq. 10 on CUDA tensors u (n, 2), inv_depth (n,), normal (n, 3) (float32).
+    Returns dict(u, inv_depth, normal, valid) of new CUDA tensors (enqueued on the stream)."""
+    import torch
+
+    n = int(inv_depth.shape[0])
+    out = dict(u=torch.empty(n, 2, device=u.device), inv_depth=torch.empty(n, device=u.device),
+               normal=torch.empty(n, 3, device=u.device), valid=torch.empty(n, dtype=torch.uint8, device=u.device))
+    s = torch.cuda.current_stream() if stream is None else stream
+    _call("sgn_transfer_surfels", _doubles(intrinsics, 4), _doubles(T_kf1_kf0, 12), n,
+          _dev(u, torch.float32, (n, 2)), _dev(inv_depth, torch.float32, (n,)), _dev(normal, torch.float32, (n, 3)),
+          out["u"].data_ptr(), out["inv_depth"].data_ptr(), out["normal"].data_ptr(), out["valid"].data_ptr(), s.cuda_stream)
+    return out
+
+
+def sgn_render_surfels(intrinsics, width, height, u, inv_depth, normal, valid, radius, zbuffer=None, stream=None):
+    """Sec. 2.2 depth-buffered render of free surfels (CUDA tensors as for sgn_transfer_surfels) of
+    the given radius.  Returns (inverse-depth map (H, W) float32, surfel index (H, W) int32)."""
+    import torch
+
+    n = int(inv_depth.shape[0])
+    dev = u.device
+    if zbuffer is None:
+        zbuffer = torch.empty(height * width, dtype=torch.int64, device=dev)
+    inv = torch.empty(height, width, device=dev)
+    sidx = torch.empty(height, width, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream() if stream is None else stream
+    _call("sgn_render_surfels", _doubles(intrinsics, 4), int(width), int(height), n, _dev(u, torch.float32, (n, 2)),
+          _dev(inv_depth, torch.float32, (n,)), _dev(normal, torch.float32, (n, 3)), _dev(valid, torch.uint8, (n,)),
+          float(radius), _dev(zbuffer, torch.int64, (height * width,)), inv.data_ptr(), sidx.data_ptr(), s.cuda_stream)
+    return inv, sidx
 
 
 def sgn_staging_timeouts() -> int:

@@ -76,13 +76,14 @@ def test_admission_by_free_memory():
     need = sgn.sgn_plan_workspace_bytes(h)
     sgn.sgn_plan_destroy(h)
     server = sgn.Server(int(1.5 * need) + (8 << 20), max_slots=4, max_surfels_per_epoch=20000)
+    # long solves, so that the later requests arrive while the first one holds the arena
     for i in range(4):
-        _submit(server, p, tag=10 + i)
+        _submit(server, p, tag=10 + i, iters=400)
     done = _collect(server)
     assert sorted(done) == [10, 11, 12, 13] and all(c.status == sgn.SGN_OK for c, _ in done.values())
     st = server.stats()
     assert st["admission_waits"] > 0 and st["peak_arena_bytes"] <= int(1.5 * need) + (8 << 20)
-    ref = gpu_solve(p, 10)
+    ref = gpu_solve(p, 400)
     m = ((done[10][1]["status"] & 0x3F) == 0) & ((ref["status"] & 0x3F) == 0)
     assert np.median(np.abs(done[10][1]["id"][m] / ref["id"][m] - 1)) < 1e-6
     big = synth.room_problem(44)  # 640x480: more than the whole arena
