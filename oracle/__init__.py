@@ -44,12 +44,12 @@ def build(force: bool = False) -> str:
 
 class Params(ctypes.Structure):
     _fields_ = [("huber_k", ctypes.c_double), ("lm_lambda", ctypes.c_double),
-                ("optimize_normal", ctypes.c_int), ("min_residuals", ctypes.c_int)]
+                ("optimize_normal", ctypes.c_int), ("min_residuals", ctypes.c_int), ("lm_adaptive", ctypes.c_int)]
 
 
 def params(huber_k: float = 9.0 / 255.0, lm_lambda: float = 1e-3, optimize_normal: bool = True,
-           min_residuals: int = 8) -> Params:
-    return Params(huber_k, lm_lambda, int(bool(optimize_normal)), int(min_residuals))
+           min_residuals: int = 8, lm_adaptive: bool = False) -> Params:
+    return Params(huber_k, lm_lambda, int(bool(optimize_normal)), int(min_residuals), int(bool(lm_adaptive)))
 
 
 _D = ctypes.POINTER(ctypes.c_double)

@@ -61,9 +61,10 @@ enum {
 
 typedef struct {
     double huber_k;
-    double lm_lambda;
+    double lm_lambda;      /* damping; the initial damping when lm_adaptive is set */
     int optimize_normal;
     int min_residuals;
+    int lm_adaptive;       /* 0: fixed lambda; 1: Marquardt schedule (see orc_gauss_newton) */
 } orc_params;
 
 typedef struct {
@@ -370,6 +371,76 @@ void orc_apply_step(const double n[3], double id_s, const double delta[3], doubl
  * depth change| over the accepted steps).
  * Returns the number of threads used.
  */
+/*
+ * One candidate step of Sec. 2.4 from (id_s, n): damped solve with the given lambda, update of n in
+ * its tangent plane and of id_s, camera-facing representative of n.  Returns the outcome code
+ * (OUT_OK when the candidate is usable).
+ */
+static int candidate_step(const orc_problem* pb, const orc_params* prm, int s, const double H[6], const double g[3],
+                          double lambda, double ids, const double ns[3], double* id_new, double n_new[3]) {
+    double delta[3];
+    if (!orc_damped_step(H, g, lambda, prm->optimize_normal, delta)) return OUT_SINGULAR;
+    if (prm->optimize_normal) {
+        orc_apply_step(ns, ids, delta, n_new, id_new);
+    } else {
+        n_new[0] = ns[0]; n_new[1] = ns[1]; n_new[2] = ns[2];
+        *id_new = ids + delta[2];
+    }
+    if (!(*id_new > 0.0) || !isfinite(*id_new) || !isfinite(n_new[0]) || !isfinite(n_new[1]) || !isfinite(n_new[2]))
+        return OUT_STEP_REJECTED;
+    double r_s[3];
+    tile_centre_ray(pb, s, r_s);
+    if (dot3(n_new, r_s) > 0.0) {
+        n_new[0] = -n_new[0]; n_new[1] = -n_new[1]; n_new[2] = -n_new[2];
+    }
+    return OUT_OK;
+}
+
+/*
+ * Levenberg-Marquardt with Marquardt's schedule (the paper names the method, Sec. 2.4, but gives
+ * no schedule): each iteration solves with the current lambda and evaluates the cost at the
+ * candidate; the candidate is accepted when the mean Huber cost over valid samples decreases
+ * (the sample set can change with the parameters), and lambda is divided by 10; otherwise the
+ * parameters stay and lambda is multiplied by 10.  A singular system or an unusable step counts
+ * as a rejection.  lambda stays in [1e-7, 1e7].  Stops when fewer than min_residuals samples are
+ * valid at the current parameters.  Returns the outcome of the last iteration and leaves H at
+ * the returned parameters.
+ */
+static int adaptive_iterations(const orc_problem* pb, const orc_params* prm, int s, int iters, double* ids,
+                               double ns[3], double H[6], double* mg, double* pn, double* pid) {
+    double g[3], E, m, lambda = prm->lm_lambda;
+    int cnt, outcome = OUT_OK;
+    orc_eval_surfel(pb, prm, s, *ids, ns, H, g, &E, &cnt, &m, NULL, NULL);
+    if (m < *mg) *mg = m;
+    for (int it = 0; it < iters; ++it) {
+        if (cnt < prm->min_residuals) return OUT_UNDERDETERMINED;
+        double id_new, n_new[3];
+        outcome = candidate_step(pb, prm, s, H, g, lambda, *ids, ns, &id_new, n_new);
+        int accept = 0;
+        double H2[6], g2[3], E2, m2;
+        int cnt2 = 0;
+        if (outcome == OUT_OK) {
+            orc_eval_surfel(pb, prm, s, id_new, n_new, H2, g2, &E2, &cnt2, &m2, NULL, NULL);
+            if (m2 < *mg) *mg = m2;
+            accept = cnt2 >= prm->min_residuals && E2 * cnt < E * cnt2;  /* E2 / cnt2 < E / cnt */
+        }
+        if (accept) {
+            *pn += acos(fmin(1.0, fabs(dot3(n_new, ns)))) * (180.0 / 3.14159265358979323846);
+            *pid += fabs(id_new / *ids - 1.0);
+            *ids = id_new;
+            ns[0] = n_new[0]; ns[1] = n_new[1]; ns[2] = n_new[2];
+            for (int i = 0; i < 6; ++i) H[i] = H2[i];
+            for (int i = 0; i < 3; ++i) g[i] = g2[i];
+            E = E2;
+            cnt = cnt2;
+            lambda = fmax(lambda / 10.0, 1e-7);
+        } else {
+            lambda = fmin(lambda * 10.0, 1e7);
+        }
+    }
+    return outcome;
+}
+
 int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthreads, double* id, double* n,
                      uint8_t* status, double* cost, int32_t* nres, double* margin, double* H_last, double* path_n,
                      double* path_id) {
@@ -402,7 +473,11 @@ int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthrea
             int cnt;
             if (H_last) for (int i = 0; i < 6; ++i) H_last[6 * s + i] = 0.0;
             double pn = 0.0, pid = 0.0;
-            for (int it = 0; it < iters; ++it) {
+            if (prm->lm_adaptive) {
+                outcome = adaptive_iterations(pb, prm, s, iters, &ids, ns, H, &mg, &pn, &pid);
+                if (H_last) for (int i = 0; i < 6; ++i) H_last[6 * s + i] = H[i];
+            }
+            for (int it = 0; it < (prm->lm_adaptive ? 0 : iters); ++it) {
                 orc_eval_surfel(pb, prm, s, ids, ns, H, g, &E, &cnt, &m, NULL, NULL);
                 if (m < mg) mg = m;
                 if (H_last) for (int i = 0; i < 6; ++i) H_last[6 * s + i] = H[i];

@@ -54,6 +54,14 @@ MUTANTS = {
     "tile centre off by half a pixel": (
         "double ux = tx * pb->P + 0.5 * (pb->P - 1), uy = ty * pb->P + 0.5 * (pb->P - 1);",
         "double ux = tx * pb->P + 0.5 * pb->P, uy = ty * pb->P + 0.5 * pb->P;"),
+    "adaptive schedule accepts a cost increase": (
+        "accept = cnt2 >= prm->min_residuals && E2 * cnt < E * cnt2;",
+        "accept = cnt2 >= prm->min_residuals && E2 * cnt > E * cnt2;"),
+    "adaptive schedule inverted": (
+        "lambda = fmax(lambda / 10.0, 1e-7);", "lambda = fmin(lambda * 10.0, 1e7);"),
+    "adaptive schedule compares total instead of mean cost": (
+        "accept = cnt2 >= prm->min_residuals && E2 * cnt < E * cnt2;",
+        "accept = cnt2 >= prm->min_residuals && E2 < E;"),
     # reference-frame change and depth-buffered render (pinned by test_oracle_transfer.py)
     "frame change with transposed rotation": (
         "p1[k] = T[4 * k] * p0[0] + T[4 * k + 1] * p0[1] + T[4 * k + 2] * p0[2] + T[4 * k + 3];",

@@ -554,3 +554,42 @@ def test_gauss_newton_minimiser_matches_brute_force_scan():
     # elongated valley of the weakest-observed normal direction at worst.
     assert np.median(d_id) <= 0.001 and max(d_id) <= 0.002
     assert np.median(d_ang) <= 0.25 and max(d_ang) <= 1.5
+
+
+def test_adaptive_lm_never_raises_the_mean_cost_and_converges():
+    """Marquardt schedule (option): accepted steps only lower the mean Huber cost, so the returned
+    mean cost is at most the initial one for every surfel; on the noise-free ring views it reaches
+    the same accuracy as the fixed damping, also from an initial lambda far too large for it."""
+    t = TOL["convergence_ring"]
+    p = synth.ring_problem(0, P=16)
+    ob = oracle.Problem.from_synth(p)
+    prm0 = oracle.params(lm_adaptive=True)
+    start = ob.solve(prm0, 0, p.id0, p.n0, p.state)
+    for lam, iters in ((1e-3, t["iterations"]), (1e3, t["iterations"] + 15)):
+        prm = oracle.params(lm_adaptive=True, lm_lambda=lam)
+        out = ob.solve(prm, iters, p.id0, p.n0, p.state)
+        live = (start["nres"] >= 8) & (out["nres"] >= 8)
+        mean0 = start["cost"][live] / start["nres"][live]
+        mean1 = out["cost"][live] / out["nres"][live]
+        assert np.all(mean1 <= mean0 * (1 + 1e-12))
+        assert np.mean(mean1 < mean0) > 0.9
+        ok = ((out["status"] & 0x3F) == oracle.OK) & (p.tile_prim >= 0)
+        assert ok.sum() > 0.85 * (p.tile_prim >= 0).sum()
+        rel = np.abs(out["id"][ok] / p.gt_id[ok] - 1)
+        ang = np.rad2deg(np.arccos(np.clip(np.abs(np.einsum("ij,ij->i", out["n"][ok], p.gt_n[ok])), 0, 1)))
+        assert np.median(rel) < t["depth_rel_median"] and np.percentile(rel, 90) < t["depth_rel_p90"]
+        assert np.median(ang) < t["normal_deg_median"] and np.percentile(ang, 90) < t["normal_deg_p90"]
+    # where steps move samples across the image border the valid-sample set changes: the schedule
+    # compares the mean cost, so it still never rises
+    q = synth.room_problem(3, W=320, H=240, F=3, seed_frac=0.0)
+    oq = oracle.Problem.from_synth(q)
+    s0 = oq.solve(prm0, 0, q.id0, q.n0, q.state)
+    s1 = oq.solve(oracle.params(lm_adaptive=True), 10, q.id0, q.n0, q.state)
+    live = (s0["nres"] >= 8) & (s1["nres"] >= 8)
+    assert np.sum(s0["nres"][live] != s1["nres"][live]) > 20
+    assert np.all(s1["cost"][live] / s1["nres"][live] <= s0["cost"][live] / s0["nres"][live] * (1 + 1e-12))
+    # a fixed damping of 1e3 barely moves in the same number of iterations
+    fixed = ob.solve(oracle.params(lm_lambda=1e3), t["iterations"] + 15, p.id0, p.n0, p.state)
+    okf = ((fixed["status"] & 0x3F) == oracle.OK) & (p.tile_prim >= 0)
+    angf = np.rad2deg(np.arccos(np.clip(np.abs(np.einsum("ij,ij->i", fixed["n"][okf], p.gt_n[okf])), 0, 1)))
+    assert np.median(angf) > 5 * t["normal_deg_median"]
