@@ -259,6 +259,48 @@ def ablation_leg(prob, stream, reps: int = 20):
     return res
 
 
+def frame_change_leg(prob, stream, reps: int = 50):
+    """Sec. 2.5 / Sec. 2.2 on the benchmark workload: the keyframe's surfels moved into the last
+    observing frame (Eq. 10) and rendered there with the depth buffer as discs of the tile's area
+    (radius P / sqrt(pi)); CUDA-event time of transfer + render (memset, splat, resolve)."""
+    import numpy as np
+    import torch
+
+    import paper_1910_01997_gb300 as sgn
+
+    TX = prob.W // prob.P
+    s = np.flatnonzero(prob.state == 1)
+    u = np.stack([(s % TX) * prob.P + (prob.P - 1) / 2.0, (s // TX) * prob.P + (prob.P - 1) / 2.0], 1)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.stream(stream):
+        d_u = torch.from_numpy(u.astype(np.float32)).to(dev)
+        d_id = torch.from_numpy(prob.id0[s].astype(np.float32)).to(dev)
+        d_n = torch.from_numpy(prob.n0[s].astype(np.float32)).to(dev)
+        zbuf = torch.empty(prob.W * prob.H, dtype=torch.int64, device=dev)
+        radius = prob.P / np.sqrt(np.pi)
+        T = prob.poses[-1]
+
+        def step():
+            out = sgn.sgn_transfer_surfels(prob.cam, T, d_u, d_id, d_n, stream=stream)
+            return sgn.sgn_render_surfels(prob.cam, prob.W, prob.H, out["u"], out["inv_depth"], out["normal"],
+                                          out["valid"], radius, zbuffer=zbuf, stream=stream)
+
+        step()
+        stream.synchronize()
+        t = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            inv, sidx = step()
+            b.record(stream)
+            b.synchronize()
+            t.append(a.elapsed_time(b))
+        drawn = int((sidx >= 0).sum().item())
+    ms = statistics.median(t)
+    return {"surfels": int(len(s)), "radius_px": float(radius), "pixels_drawn": drawn, "ms": ms,
+            "surfels_per_s": len(s) / (ms * 1e-3), "note": "transfer (Eq. 10) + depth-buffered disc render, 4 launches"}
+
+
 def serving_leg(duration_s: float, dev, streams: int = 16, rate_hz: float = 5.0, burst: int = 96):
     """Config-5 leg: 16 simulated camera streams submit keyframe solves (Poisson arrivals, 5/s per
     stream; half 640x480, half 1280x720; 8x8 surfels, 4 frames, FP16 texels, 10 iterations) to the
@@ -539,6 +581,7 @@ def run_ours(args):
     if rank == 0 and not args.no_batch:
         line["batch"] = [batch_leg(dt, stream, dev) for dt in ("f32", "f16")]
         line["ablation"] = ablation_leg(prob, stream)
+        line["frame_change"] = frame_change_leg(prob, stream)
     if rank == 0 and args.serve_seconds > 0:
         line["serving"] = serving_leg(args.serve_seconds, dev)
     if rank == 0 and not args.no_cpu_baseline:

@@ -42,7 +42,7 @@ extern "C" {
 #endif
 
 #define SGN_MAX_FRAMES 16
-#define SGN_ABI_VERSION 1
+#define SGN_ABI_VERSION 2
 
 typedef enum {
     SGN_OK = 0,
@@ -83,6 +83,11 @@ typedef struct {
     double fp64_cond;         /* solve in FP64 when cond2 of the Jacobi-scaled H exceeds this; <= 0: never; default 1e6 */
     int optimize_normal;      /* 1; 0 = depth-only ablation (d id_u / d n := 0, Sec. 4.4) */
     int min_residuals;        /* fewer valid samples than this: no update; default 8 */
+    int lm_adaptive;          /* 0 (default): fixed damping lm_lambda.  1: Marquardt schedule starting at
+                                 lm_lambda: a step is kept when the mean Huber cost over valid samples
+                                 decreases (lambda / 10), otherwise dropped (lambda x 10); a singular system
+                                 or an unusable step counts as dropped; lambda stays in [1e-7, 1e7]; one
+                                 extra cost evaluation per solve */
 } sgn_plan_desc;
 
 typedef struct sgn_plan sgn_plan;     /* opaque, host side */

@@ -80,7 +80,7 @@ def _load():
                                            ctypes.POINTER(c_i), _D, _D, _D]),
                 "orc_damped_step": (c_i, [_D, _D, c_d, c_i, _D]),
                 "orc_apply_step": (None, [_D, c_d, _D, _D, _D]),
-                "orc_gauss_newton": (c_i, [_V, ctypes.POINTER(Params), c_i, c_i, _D, _D, _V, _D, _V, _V, _V, _V, _V]),
+                "orc_gauss_newton": (c_i, [_V, ctypes.POINTER(Params), c_i, c_i, _D, _D, _V, _D, _V, _V, _V, _V, _V, _V]),
                 "orc_problem_create_planes": (_V, [c_i, c_i, c_i, c_d, c_d, c_d, c_d, _V, c_i, _D, _D, _D, _D]),
                 "orc_seed": (None, [_V, _D, _D, _V, _D, _D, _V]),
                 "orc_depth_map": (None, [_V, _D, _D, _V, _D, _V]),
@@ -308,15 +308,17 @@ class Problem:
         H_last = np.empty(6 * self.S) if diagnostics else None
         path_n = np.empty(self.S) if diagnostics else None
         path_id = np.empty(self.S) if diagnostics else None
+        dmargin = np.empty(self.S) if diagnostics else None
         used = _load().orc_gauss_newton(self._h, ctypes.byref(prm), int(iters), int(nthreads), _d(id_s), _d(n),
                                         _v(status), _d(cost), _v(nres), _v(margin), _v(H_last), _v(path_n),
-                                        _v(path_id))
+                                        _v(path_id), _v(dmargin))
         out = dict(id=id_s, n=n.reshape(-1, 3), status=status, cost=cost, nres=nres, threads=used)
         if diagnostics:
             out["margin"] = margin
             out["H_last"] = H_last.reshape(-1, 6)
             out["path_n"] = path_n
             out["path_id"] = path_id
+            out["decision_margin"] = dmargin
         return out
 
     def depth_map(self, id_s, n, status):

@@ -368,7 +368,9 @@ void orc_apply_step(const double n[3], double id_s, const double delta[3], doubl
  * diagnostics: margin (smallest distance of any sample used to the validity bounds,
  * over all evaluations), H_last (6 per surfel, undamped H of the last iteration), path_n (sum of
  * the normal's rotation over the accepted steps, degrees) and path_id (sum of |relative inverse
- * depth change| over the accepted steps).
+ * depth change| over the accepted steps), decision_margin (with lm_adaptive: the smallest relative
+ * difference |mean cost of a candidate - mean cost at the current parameters| / current, over the
+ * surfel's accept/reject decisions; infinite otherwise).
  * Returns the number of threads used.
  */
 /*
@@ -407,7 +409,7 @@ static int candidate_step(const orc_problem* pb, const orc_params* prm, int s, c
  * the returned parameters.
  */
 static int adaptive_iterations(const orc_problem* pb, const orc_params* prm, int s, int iters, double* ids,
-                               double ns[3], double H[6], double* mg, double* pn, double* pid) {
+                               double ns[3], double H[6], double* mg, double* pn, double* pid, double* dm) {
     double g[3], E, m, lambda = prm->lm_lambda;
     int cnt, outcome = OUT_OK;
     orc_eval_surfel(pb, prm, s, *ids, ns, H, g, &E, &cnt, &m, NULL, NULL);
@@ -423,6 +425,10 @@ static int adaptive_iterations(const orc_problem* pb, const orc_params* prm, int
             orc_eval_surfel(pb, prm, s, id_new, n_new, H2, g2, &E2, &cnt2, &m2, NULL, NULL);
             if (m2 < *mg) *mg = m2;
             accept = cnt2 >= prm->min_residuals && E2 * cnt < E * cnt2;  /* E2 / cnt2 < E / cnt */
+            if (cnt2 >= prm->min_residuals && E > 0.0) {  /* relative distance of the decision from a tie */
+                const double d = fabs(E2 * cnt - E * cnt2) / (E * cnt2);
+                if (d < *dm) *dm = d;
+            }
         }
         if (accept) {
             *pn += acos(fmin(1.0, fabs(dot3(n_new, ns)))) * (180.0 / 3.14159265358979323846);
@@ -443,7 +449,7 @@ static int adaptive_iterations(const orc_problem* pb, const orc_params* prm, int
 
 int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthreads, double* id, double* n,
                      uint8_t* status, double* cost, int32_t* nres, double* margin, double* H_last, double* path_n,
-                     double* path_id) {
+                     double* path_id, double* decision_margin) {
     const orc_problem* pb = (const orc_problem*)p;
     int S = (pb->W / pb->P) * (pb->H / pb->P);
     int used = 1;
@@ -459,6 +465,7 @@ int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthrea
             int st = status[s] & 0x3f;
             int flags = status[s] & OUT_SEEDED_FLAG;
             double mg = INFINITY;
+            if (decision_margin) decision_margin[s] = INFINITY;
             if (st == OUT_EMPTY || st == OUT_UNSEEDED) {
                 cost[s] = 0.0;
                 nres[s] = 0;
@@ -474,7 +481,9 @@ int orc_gauss_newton(const void* p, const orc_params* prm, int iters, int nthrea
             if (H_last) for (int i = 0; i < 6; ++i) H_last[6 * s + i] = 0.0;
             double pn = 0.0, pid = 0.0;
             if (prm->lm_adaptive) {
-                outcome = adaptive_iterations(pb, prm, s, iters, &ids, ns, H, &mg, &pn, &pid);
+                double dm = INFINITY;
+                outcome = adaptive_iterations(pb, prm, s, iters, &ids, ns, H, &mg, &pn, &pid, &dm);
+                if (decision_margin) decision_margin[s] = dm;
                 if (H_last) for (int i = 0; i < 6; ++i) H_last[6 * s + i] = H[i];
             }
             for (int it = 0; it < (prm->lm_adaptive ? 0 : iters); ++it) {

@@ -209,6 +209,7 @@ PlanParams make_params(const sgn_plan* p) {
     pp.fp64_cond = d.fp64_cond > 0 ? float(std::min(d.fp64_cond, 3.0e38)) : 0.0f;
     pp.optimize_normal = d.optimize_normal;
     pp.min_residuals = d.min_residuals;
+    pp.lm_adaptive = d.lm_adaptive;
     char* b = p->ws;
     const Layout& L = p->L;
     pp.kf = reinterpret_cast<const float*>(b + L.kf);
@@ -299,6 +300,7 @@ sgn_status sgn_plan_desc_default(sgn_plan_desc* d, int width, int height, int pa
     d->fp64_cond = 1e6;
     d->optimize_normal = 1;
     d->min_residuals = 8;
+    d->lm_adaptive = 0;
     return SGN_OK;
 }
 
@@ -318,6 +320,7 @@ sgn_status sgn_plan_create(const sgn_plan_desc* d, sgn_plan** out) {
     if (std::isnan(d->fp64_cond)) return fail(SGN_ERR_INVALID_ARGUMENT, "fp64_cond is NaN");
     if (d->optimize_normal != 0 && d->optimize_normal != 1) return fail(SGN_ERR_INVALID_ARGUMENT, "optimize_normal must be 0 or 1");
     if (d->min_residuals < 0) return fail(SGN_ERR_INVALID_ARGUMENT, "min_residuals must be >= 0");
+    if (d->lm_adaptive != 0 && d->lm_adaptive != 1) return fail(SGN_ERR_INVALID_ARGUMENT, "lm_adaptive must be 0 or 1");
     sgn_plan* p = new (std::nothrow) sgn_plan();
     if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "out of host memory");
     p->desc = *d;

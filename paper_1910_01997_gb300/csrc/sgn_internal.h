@@ -57,6 +57,7 @@ struct PlanParams {
     float fp64_cond;    // <= 0: never route to FP64
     int optimize_normal;
     int min_residuals;
+    int lm_adaptive;    // Marquardt schedule (see sgn_plan_desc)
     // device buffers (inside the plan's workspace)
     const float* kf;            // keyframe intensity, H rows of kf_pitch floats
     int kf_pitch;

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(sgn):
 def test_library_has_no_dynamic_cuda_runtime_dependency(sgn):
     # statically linked cudart: the library loads on hosts without a CUDA runtime in the loader path
     ctypes.CDLL(sgn.LIB_PATH)
-    assert sgn.sgn_abi_version() == 1
+    assert sgn.sgn_abi_version() == 2
 
 
 def test_desc_defaults_and_validation(sgn):
@@ -52,7 +52,7 @@ def test_desc_defaults_and_validation(sgn):
     sgn.sgn_plan_destroy(h)
     bad = [("patch", 5), ("patch", 32), ("width", 4), ("height", 20000), ("max_frames", 0), ("max_frames", 17),
            ("image_dtype", 7), ("huber_k", 0.0), ("huber_k", float("nan")), ("lm_lambda", -1.0),
-           ("optimize_normal", 2), ("min_residuals", -1), ("fp64_cond", float("nan"))]
+           ("optimize_normal", 2), ("min_residuals", -1), ("fp64_cond", float("nan")), ("lm_adaptive", 3)]
     for field, value in bad:
         d2 = sgn.sgn_plan_desc_default(640, 480, 8, 5)
         setattr(d2, field, value)
