@@ -44,12 +44,14 @@ def build(force: bool = False) -> str:
 
 class Params(ctypes.Structure):
     _fields_ = [("huber_k", ctypes.c_double), ("lm_lambda", ctypes.c_double),
-                ("optimize_normal", ctypes.c_int), ("min_residuals", ctypes.c_int), ("lm_adaptive", ctypes.c_int)]
+                ("optimize_normal", ctypes.c_int), ("min_residuals", ctypes.c_int), ("lm_adaptive", ctypes.c_int),
+                ("radius", ctypes.c_double)]
 
 
 def params(huber_k: float = 9.0 / 255.0, lm_lambda: float = 1e-3, optimize_normal: bool = True,
-           min_residuals: int = 8, lm_adaptive: bool = False) -> Params:
-    return Params(huber_k, lm_lambda, int(bool(optimize_normal)), int(min_residuals), int(bool(lm_adaptive)))
+           min_residuals: int = 8, lm_adaptive: bool = False, radius: float = 0.0) -> Params:
+    return Params(huber_k, lm_lambda, int(bool(optimize_normal)), int(min_residuals), int(bool(lm_adaptive)),
+                  float(radius))
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -334,7 +336,16 @@ class Problem:
         """The whole path: seeding (Sec. 2.3), Gauss-Newton (Sec. 2.4), final cost, depth map (Sec. 2.2)."""
         id_s, n, status = self.seed(id0, n0, state)
         out = self.gauss_newton(prm, iters, id_s, n, status, nthreads)
-        if depth_map:
+        if depth_map and prm.radius > 0:
+            # circular surfels may overlap: the depth-buffered render of the discs (Sec. 2.2)
+            TX = self.W // self.P
+            s = np.arange(self.S)
+            u = np.stack([(s % TX) * self.P + (self.P - 1) / 2.0, (s // TX) * self.P + (self.P - 1) / 2.0], 1)
+            st = out["status"] & 0x3F
+            drawn = ((st != EMPTY) & (st != UNSEEDED)).astype(np.uint8)
+            out["inv_depth"], out["sidx"] = render_surfels(self.cam, self.W, self.H, u, out["id"], out["n"], drawn,
+                                                           prm.radius)
+        elif depth_map:
             out["inv_depth"], out["sidx"] = self.depth_map(out["id"], out["n"], out["status"])
         out["seeded_id"], out["seeded_n"], out["seeded_status"] = id_s, n, status
         return out

@@ -38,7 +38,10 @@
  *  - reference-frame change (Sec. 2.5, Eq. 10) and the depth-buffered render of
  *    free surfels (Sec. 2.2, Eq. 3 and Eq. 4): a surfel covers the pixels whose
  *    centre is within radius r of its projected point; the nearest wins and
- *    equal inverse depths go to the lower surfel index.
+ *    equal inverse depths go to the lower surfel index;
+ *  - circular surfels (option radius > 0): surfel s is the set of pixels within
+ *    the radius of its tile centre (Eq. 4); neighbouring discs may overlap, and
+ *    the depth map is then the depth-buffered render of the discs.
  *
  * Parity pins: every function below is pinned by a test in tests/ against
  * closed forms, finite differences, library routines or brute force; the
@@ -65,6 +68,8 @@ typedef struct {
     int optimize_normal;
     int min_residuals;
     int lm_adaptive;       /* 0: fixed lambda; 1: Marquardt schedule (see orc_gauss_newton) */
+    double radius;         /* 0: surfel s is its P x P tile; > 0: the pixels within this radius of
+                              the tile centre (Eq. 4), inside the image */
 } orc_params;
 
 typedef struct {
@@ -278,9 +283,21 @@ void orc_eval_surfel(const void* p, const orc_params* prm, int s, double id_s, c
     *E = 0.0;
     *cnt = 0;
     double mg = INFINITY;
-    for (int py = 0; py < P; ++py)
-        for (int px = 0; px < P; ++px) {
-            int ux = tx * P + px, uy = ty * P + py;
+    /* the surfel's pixels: its tile, or the pixels whose centre lies strictly within the radius of
+     * the tile centre (Eq. 4) */
+    const double ucx = tx * P + 0.5 * (P - 1), ucy = ty * P + 0.5 * (P - 1), rad = prm->radius;
+    int x0 = tx * P, x1 = tx * P + P - 1, y0 = ty * P, y1 = ty * P + P - 1;
+    if (rad > 0.0) {
+        x0 = (int)floor(ucx - rad); x1 = (int)ceil(ucx + rad);
+        y0 = (int)floor(ucy - rad); y1 = (int)ceil(ucy + rad);
+        if (x0 < 0) x0 = 0;
+        if (y0 < 0) y0 = 0;
+        if (x1 > W - 1) x1 = W - 1;
+        if (y1 > Hh - 1) y1 = Hh - 1;
+    }
+    for (int uy = y0; uy <= y1; ++uy)
+        for (int ux = x0; ux <= x1; ++ux) {
+            if (rad > 0.0 && !(sqrt((ux - ucx) * (ux - ucx) + (uy - ucy) * (uy - ucy)) < rad)) continue;
             double r_u[3];
             orc_ray(pb->fx, pb->fy, pb->cx, pb->cy, ux, uy, r_u);
             double id_u = orc_inv_depth(r_u, r_s, id_s, n);

@@ -28,7 +28,8 @@ def gpu_solve(prob, iters, dtype="f32", lanes=0, block=0, steps=None, **opts):
 
 
 def oracle_params(**opts):
-    keep = {k: opts[k] for k in ("huber_k", "lm_lambda", "optimize_normal", "min_residuals", "lm_adaptive") if k in opts}
+    keep = {k: opts[k] for k in ("huber_k", "lm_lambda", "optimize_normal", "min_residuals", "lm_adaptive", "radius")
+            if k in opts}
     return oracle.params(**keep)
 
 

@@ -62,6 +62,12 @@ MUTANTS = {
     "adaptive schedule compares total instead of mean cost": (
         "accept = cnt2 >= prm->min_residuals && E2 * cnt < E * cnt2;",
         "accept = cnt2 >= prm->min_residuals && E2 < E;"),
+    "circular surfel boundary inclusive": (
+        "if (rad > 0.0 && !(sqrt((ux - ucx) * (ux - ucx) + (uy - ucy) * (uy - ucy)) < rad)) continue;",
+        "if (rad > 0.0 && !(sqrt((ux - ucx) * (ux - ucx) + (uy - ucy) * (uy - ucy)) <= rad)) continue;"),
+    "circular surfel centred on the tile corner": (
+        "const double ucx = tx * P + 0.5 * (P - 1), ucy = ty * P + 0.5 * (P - 1), rad = prm->radius;",
+        "const double ucx = tx * P, ucy = ty * P, rad = prm->radius;"),
     # reference-frame change and depth-buffered render (pinned by test_oracle_transfer.py)
     "frame change with transposed rotation": (
         "p1[k] = T[4 * k] * p0[0] + T[4 * k + 1] * p0[1] + T[4 * k + 2] * p0[2] + T[4 * k + 3];",

@@ -593,3 +593,55 @@ def test_adaptive_lm_never_raises_the_mean_cost_and_converges():
     okf = ((fixed["status"] & 0x3F) == oracle.OK) & (p.tile_prim >= 0)
     angf = np.rad2deg(np.arccos(np.clip(np.abs(np.einsum("ij,ij->i", fixed["n"][okf], p.gt_n[okf])), 0, 1)))
     assert np.median(angf) > 5 * t["normal_deg_median"]
+
+
+def test_circular_surfel_pixels_and_cost_gradient():
+    """Circular surfels (radius option, Eq. 4): an interior surfel with every sample valid uses
+    exactly the pixels strictly inside the radius of its tile centre (brute-force lattice count, F
+    samples each), and on exact (linear) frames g is still the gradient of its Huber cost."""
+    cam, ob, _, _ = _linear_problem(W=64, H=56)
+    TX = 64 // 8
+    for radius in (3.0, 4.2, 6.5, np.sqrt(6.5)):  # sqrt(6.5): pixels at (0.5, 2.5) sit on the boundary
+        prm = oracle.params(huber_k=1e9, radius=radius)
+        s = 3 * TX + 3  # tile (3, 3): centre (27.5, 27.5), the disc stays inside the image
+        ux, uy = 3 * 8 + 3.5, 3 * 8 + 3.5
+        yy, xx = np.mgrid[0:56, 0:64]
+        count = int((np.sqrt((xx - ux) * (xx - ux) + (yy - uy) * (yy - uy)) < radius).sum())
+        r_s = oracle.ray(cam, ux, uy)
+        n0 = np.array([0.1, -0.05, -1.0]) / np.linalg.norm([0.1, -0.05, -1.0])
+        e = ob.eval_surfel(prm, s, 0.5, n0)
+        assert e["cnt"] == 2 * count and e["margin"] > 1e-3
+        fd = _theta_fd(ob, prm, s, 0.5, n0, 1e-6, lambda q: q["E"])
+        assert np.allclose(e["g"], fd, rtol=1e-5, atol=1e-9 * np.abs(e["g"]).max()), (radius, e["g"], fd)
+    # the smallest disc: the four pixels nearest to the (half-integer) centre
+    d = ob.eval_surfel(oracle.params(huber_k=1e9, radius=0.75), s, 0.5, n0)
+    assert d["cnt"] == 2 * 4
+
+
+def test_circular_surfels_converge_and_render():
+    """Noise-free ring views with discs of radius 10 around 16-px tile centres (overlapping): the
+    solve reaches the same accuracy as with tiles, and the depth map is the depth-buffered render
+    of the discs, so every drawn pixel lies on the plane of the surfel that drew it."""
+    t = TOL["convergence_ring"]
+    p = synth.ring_problem(0, P=16)
+    ob = oracle.Problem.from_synth(p)
+    out = ob.solve(oracle.params(radius=10.0), t["iterations"], p.id0, p.n0, p.state)
+    ok = ((out["status"] & 0x3F) == oracle.OK) & (p.tile_prim >= 0)
+    assert ok.sum() > 0.85 * (p.tile_prim >= 0).sum()
+    rel = np.abs(out["id"][ok] / p.gt_id[ok] - 1)
+    ang = np.rad2deg(np.arccos(np.clip(np.abs(np.einsum("ij,ij->i", out["n"][ok], p.gt_n[ok])), 0, 1)))
+    assert np.median(rel) < t["depth_rel_median"] and np.median(ang) < t["normal_deg_median"]
+    sidx = out["sidx"]
+    m = sidx >= 0
+    yy, xx = np.mgrid[0:p.H, 0:p.W]
+    s = sidx[m]
+    TX = p.W // p.P
+    ux, uy = (s % TX) * 16 + 7.5, (s // TX) * 16 + 7.5
+    assert np.all(np.hypot(xx[m] - ux, yy[m] - uy) < 10.0)
+    cam = p.cam
+    r_u = np.stack([(xx[m] - cam[2]) / cam[0], (yy[m] - cam[3]) / cam[1], np.ones(m.sum())], 1)
+    r_s = np.stack([(ux - cam[2]) / cam[0], (uy - cam[3]) / cam[1], np.ones(m.sum())], 1)
+    nn = out["n"][s]
+    assert np.allclose(np.einsum("ij,ij->i", r_u / out["inv_depth"][m][:, None], nn),
+                       np.einsum("ij,ij->i", r_s / out["id"][s][:, None], nn), rtol=1e-10)
+    assert m.mean() > 0.9  # radius 10 > 16 / sqrt(2): discs cover the tiled area
