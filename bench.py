@@ -212,9 +212,10 @@ def batch_leg(dtype: str, stream, dev, reps: int = 5):
 
 
 def ablation_leg(prob, stream, reps: int = 20):
-    """Depth-only ablation (Sec. 4.4) on the benchmark workload: the same solve with the normal
-    optimised and with d id_u / d n = 0, each scored against the scene's ground truth (per-pixel
-    inverse depth of the returned map, per-surfel normal angle) and timed (Gauss-Newton launch)."""
+    """Variants of the method on the benchmark workload, each scored against the scene's ground
+    truth (per-pixel inverse depth of the returned map, per-surfel normal angle) and timed (whole
+    solve): the default; the depth-only ablation (Sec. 4.4, d id_u / d n = 0); Levenberg-Marquardt
+    with Marquardt's schedule; circular surfels of the tile's area (radius P / sqrt(pi), Eq. 4)."""
     import numpy as np
     import torch
 
@@ -224,8 +225,10 @@ def ablation_leg(prob, stream, reps: int = 20):
     iters = WORKLOAD["iterations"]
     res = {}
     with torch.cuda.stream(stream):
-        for name, opt_n in (("full", True), ("depth_only", False)):
-            plan = sgn.Plan(prob.W, prob.H, prob.P, prob.F, WORKLOAD["texels"], stream=stream, optimize_normal=opt_n)
+        variants = (("full", {}), ("depth_only", {"optimize_normal": False}), ("adaptive_lm", {"lm_adaptive": True}),
+                    ("circular", {"surfel_radius": float(prob.P / np.sqrt(np.pi))}))
+        for name, opts in variants:
+            plan = sgn.Plan(prob.W, prob.H, prob.P, prob.F, WORKLOAD["texels"], stream=stream, **opts)
             plan.set_intrinsics(*prob.cam)
             plan.set_keyframe(prob.keyframe)
             plan.set_frames(prob.frames, prob.poses)

@@ -88,6 +88,13 @@ typedef struct {
                                  decreases (lambda / 10), otherwise dropped (lambda x 10); a singular system
                                  or an unusable step counts as dropped; lambda stays in [1e-7, 1e7]; one
                                  extra cost evaluation per solve */
+    float surfel_radius;      /* 0 (default): surfel s is its P x P tile.  In [0.5, 16]: surfel s is the set
+                                 of pixels whose centre lies strictly within this radius of its tile centre
+                                 (the paper's circular surfel, Eq. 4; at most 512 pixels); discs of
+                                 neighbouring tiles may overlap, and the depth map is then the
+                                 depth-buffered render of the discs (Sec. 2.2, as sgn_render_surfels).
+                                 Such plans use 32 lanes per surfel and cannot join a batch, a server or
+                                 sgn_solve_static */
 } sgn_plan_desc;
 
 typedef struct sgn_plan sgn_plan;     /* opaque, host side */

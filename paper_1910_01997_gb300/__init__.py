@@ -39,7 +39,7 @@ class sgn_plan_desc(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("patch", ctypes.c_int),
                 ("max_frames", ctypes.c_int), ("image_dtype", ctypes.c_int), ("huber_k", ctypes.c_float),
                 ("lm_lambda", ctypes.c_float), ("fp64_cond", ctypes.c_double), ("optimize_normal", ctypes.c_int),
-                ("min_residuals", ctypes.c_int), ("lm_adaptive", ctypes.c_int)]
+                ("min_residuals", ctypes.c_int), ("lm_adaptive", ctypes.c_int), ("surfel_radius", ctypes.c_float)]
 
 
 class sgn_request(ctypes.Structure):
@@ -468,7 +468,8 @@ class Plan:
     """A plan plus its device workspace (a torch uint8 tensor) on the current CUDA device/stream."""
 
     def __init__(self, width, height, patch, max_frames, image_dtype="f32", *, huber_k=9.0 / 255.0,
-                 lm_lambda=1e-3, fp64_cond=1e6, optimize_normal=True, min_residuals=8, lm_adaptive=False, stream=None,
+                 lm_lambda=1e-3, fp64_cond=1e6, optimize_normal=True, min_residuals=8, lm_adaptive=False,
+                 surfel_radius=0.0, stream=None,
                  lanes_per_surfel=0, block_threads=0, staging=False):
         torch = _torch()
         d = sgn_plan_desc_default(width, height, patch, max_frames)
@@ -476,6 +477,7 @@ class Plan:
         d.huber_k, d.lm_lambda, d.fp64_cond = huber_k, lm_lambda, fp64_cond
         d.optimize_normal, d.min_residuals = int(bool(optimize_normal)), min_residuals
         d.lm_adaptive = int(bool(lm_adaptive))
+        d.surfel_radius = float(surfel_radius)
         self.desc = d
         self.handle = sgn_plan_create(d)
         self.W, self.H, self.P = width, height, patch

@@ -61,12 +61,12 @@ struct DeviceGuard {
 };
 
 struct Layout {
-    size_t kf, tex, raw, id0, n0, state0, id, n, cost, nres, status, depth, sidx, total;
+    size_t kf, tex, raw, id0, n0, state0, id, n, cost, nres, status, depth, sidx, disc, zbuf, total;
     int kf_pitch, tex_pitch, raw_pitch;
     long long tex_plane, raw_plane;
 };
 
-Layout make_layout(const sgn_plan_desc& d, int S) {
+Layout make_layout(const sgn_plan_desc& d, int S, int disc_n) {
     Layout L{};
     const size_t W = size_t(d.width), H = size_t(d.height);
     L.kf_pitch = int(round_up(W, 64));
@@ -93,6 +93,10 @@ Layout make_layout(const sgn_plan_desc& d, int S) {
     L.status = take(size_t(S));
     L.depth = take(W * H * sizeof(float));
     L.sidx = take(W * H * sizeof(int32_t));
+    if (disc_n > 0) {  // circular surfels: pixel table and the depth buffer of the disc render
+        L.disc = take(size_t(disc_n) * 2 * sizeof(int));
+        L.zbuf = take(W * H * sizeof(unsigned long long));
+    }
     L.total = off;
     return L;
 }
@@ -148,6 +152,7 @@ struct sgn_plan {
     bool state_pending = false;  // initial surfels uploaded, working state not derived yet
     bool depth_valid = false;
     int lanes = 0, block = 256;
+    std::vector<int> disc;                // circular surfels: pixel offsets (x, y) from the tile origin
     bool staging = false;                 // stage texel boxes in shared memory (TMA)
     alignas(64) unsigned char tmap[sgn::kTensorMapBytes] = {};
     bool tmap_ok = false;                 // tmap describes the bound workspace's texel planes
@@ -228,6 +233,10 @@ PlanParams make_params(const sgn_plan* p) {
     pp.depth = reinterpret_cast<float*>(b + L.depth);
     pp.sidx = reinterpret_cast<int32_t*>(b + L.sidx);
     pp.stage_err = sgn::stage_error_word();
+    pp.radius = d.surfel_radius;
+    pp.disc_n = int(p->disc.size() / 2);
+    pp.disc = pp.disc_n ? reinterpret_cast<const int*>(b + L.disc) : nullptr;
+    pp.zbuf = pp.disc_n ? reinterpret_cast<unsigned long long*>(b + L.zbuf) : nullptr;
     for (int f = 0; f < p->F; ++f) {
         for (int i = 0; i < 3; ++i) {
             for (int j = 0; j < 3; ++j) {
@@ -301,6 +310,7 @@ sgn_status sgn_plan_desc_default(sgn_plan_desc* d, int width, int height, int pa
     d->optimize_normal = 1;
     d->min_residuals = 8;
     d->lm_adaptive = 0;
+    d->surfel_radius = 0.0f;
     return SGN_OK;
 }
 
@@ -321,14 +331,24 @@ sgn_status sgn_plan_create(const sgn_plan_desc* d, sgn_plan** out) {
     if (d->optimize_normal != 0 && d->optimize_normal != 1) return fail(SGN_ERR_INVALID_ARGUMENT, "optimize_normal must be 0 or 1");
     if (d->min_residuals < 0) return fail(SGN_ERR_INVALID_ARGUMENT, "min_residuals must be >= 0");
     if (d->lm_adaptive != 0 && d->lm_adaptive != 1) return fail(SGN_ERR_INVALID_ARGUMENT, "lm_adaptive must be 0 or 1");
+    std::vector<int> disc;
+    if (d->surfel_radius != 0.0f) {
+        if (!(d->surfel_radius >= 0.5f) || !(d->surfel_radius <= 16.0f))
+            return fail(SGN_ERR_INVALID_ARGUMENT, "surfel_radius must be 0 (tiles) or in [0.5, 16]");
+        const int n = sgn::disc_pixels(d->patch, d->surfel_radius, nullptr);
+        if (n < 1) return fail(SGN_ERR_INVALID_ARGUMENT, "surfel_radius %g covers more than %d pixels", double(d->surfel_radius), sgn::kMaxDiscPixels);
+        disc.resize(size_t(2) * n);
+        sgn::disc_pixels(d->patch, d->surfel_radius, disc.data());
+    }
     sgn_plan* p = new (std::nothrow) sgn_plan();
     if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "out of host memory");
     p->desc = *d;
     p->TX = d->width / d->patch;
     p->TY = d->height / d->patch;
     p->S = p->TX * p->TY;
-    p->L = make_layout(*d, p->S);
-    p->lanes = default_lanes(d->patch);
+    p->disc = std::move(disc);
+    p->L = make_layout(*d, p->S, int(p->disc.size() / 2));
+    p->lanes = p->disc.empty() ? default_lanes(d->patch) : 32;
     *out = p;
     return SGN_OK;
 }
@@ -357,9 +377,12 @@ sgn_status sgn_plan_workspace_bytes(const sgn_plan* p, size_t* bytes) {
 
 sgn_status sgn_plan_set_mapping(sgn_plan* p, int lanes_per_surfel, int block_threads) {
     if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "plan is NULL");
-    const int G = lanes_per_surfel ? lanes_per_surfel : default_lanes(p->desc.patch);
+    const int G = lanes_per_surfel ? lanes_per_surfel : (p->disc.empty() ? default_lanes(p->desc.patch) : 32);
     const int B = block_threads ? block_threads : 256;
-    if (!mapping_supported(p->desc.patch, G)) return fail(SGN_ERR_INVALID_ARGUMENT, "%d lanes per surfel not supported for %dx%d tiles", G, p->desc.patch, p->desc.patch);
+    if (!p->disc.empty() && lanes_per_surfel && G != 32)
+        return fail(SGN_ERR_INVALID_ARGUMENT, "circular surfels use 32 lanes per surfel");
+    if (p->disc.empty() && !mapping_supported(p->desc.patch, G))
+        return fail(SGN_ERR_INVALID_ARGUMENT, "%d lanes per surfel not supported for %dx%d tiles", G, p->desc.patch, p->desc.patch);
     if (B < 32 || B > 256 || B % 32) return fail(SGN_ERR_INVALID_ARGUMENT, "block_threads must be a multiple of 32 in [32, 256]");
     p->lanes = G;
     p->block = B;
@@ -418,6 +441,9 @@ sgn_status sgn_plan_bind(sgn_plan* p, void* ws, size_t bytes, void* stream) {
     const size_t npx = size_t(p->desc.width) * p->desc.height;
     e = cudaMemsetAsync(p->ws + p->L.depth, 0, npx * sizeof(float), p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->ws + p->L.sidx, 0xff, npx * sizeof(int32_t), p->stream);
+    if (e == cudaSuccess && !p->disc.empty())  // the plan owns the host table, which outlives the copy
+        e = cudaMemcpyAsync(p->ws + p->L.disc, p->disc.data(), p->disc.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the depth map");
     p->depth_valid = true;
     return SGN_OK;
@@ -597,9 +623,14 @@ static sgn_status run_mode(sgn_plan* p, int iters, int mode) {
         if (te) return cuda_fail(te, "encoding the texel TMA descriptor");
         p->tmap_ok = true;
     }
-    int e = sgn::launch_gn(pp, iters, mode, p->lanes, p->block, p->stream, p->staging ? p->tmap : nullptr);
+    const bool disc = !p->disc.empty();
+    int e = sgn::launch_gn(pp, iters, mode, p->lanes, p->block, p->stream, p->staging && !disc ? p->tmap : nullptr);
     if (e) return cuda_fail(e, "Gauss-Newton launch");
     sgn::count_launch();
+    if (disc) {  // overlapping discs: the depth map is their depth-buffered render (Sec. 2.2)
+        if ((e = sgn::launch_render_discs(pp, p->stream))) return cuda_fail(e, "disc render launch");
+        sgn::count_launch(2);
+    }
     p->state_pending = false;  // a solve writes the whole working state
     p->depth_valid = true;
     return SGN_OK;
@@ -636,9 +667,9 @@ sgn_status sgn_read_depth_map(sgn_plan* p, float* inv_depth, int32_t* sidx, sgn_
         if (!p->have_K || !p->surfels_set) return fail(SGN_ERR_STATE, "depth map needs intrinsics and surfels");
         if ((st = ensure_state(p)) != SGN_OK) return st;
         PlanParams pp = make_params(p);
-        int e = sgn::launch_render_depth(pp, p->stream);
+        int e = p->disc.empty() ? sgn::launch_render_depth(pp, p->stream) : sgn::launch_render_discs(pp, p->stream);
         if (e) return cuda_fail(e, "depth render launch");
-        sgn::count_launch();
+        sgn::count_launch(p->disc.empty() ? 1 : 2);
         p->depth_valid = true;
     }
     const size_t npx = size_t(p->desc.width) * p->desc.height;
@@ -724,6 +755,7 @@ static void batch_drop_graph(sgn_batch* b) {
 sgn_status sgn_batch_add(sgn_batch* b, sgn_plan* p) {
     if (!b || !p) return fail(SGN_ERR_INVALID_ARGUMENT, "batch/plan is NULL");
     if (int(b->plans.size()) >= b->max_plans) return fail(SGN_ERR_INVALID_ARGUMENT, "batch is full (%d plans)", b->max_plans);
+    if (!p->disc.empty()) return fail(SGN_ERR_INVALID_ARGUMENT, "circular surfels are solved per plan, not in a batch");
     b->plans.push_back(p);
     b->dirty = true;
     return SGN_OK;

@@ -104,18 +104,11 @@ __global__ void __launch_bounds__(256) k_transfer_surfels(const Cam cam, const P
     valid[i] = ok ? 1 : 0;
 }
 
-// One warp per surfel: the lanes sweep the pixel box around the disc of radius r.  Eq. 3 is taken in
-// the tile-local form id_u = id_s (1 + ((r_u - r_s) . n) / (r_s . n)), which has no cancellation for
-// pixels near the surfel's centre.
-__global__ void __launch_bounds__(256) k_render_surfels(const Cam cam, int W, int H, int n, const float2* __restrict__ u,
-                                                        const float* __restrict__ id, const float* __restrict__ nrm,
-                                                        const uint8_t* __restrict__ valid, float radius,
-                                                        unsigned long long* __restrict__ zbuf) {
-    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
-    if (i >= n || !valid[i]) return;
-    const float2 us = u[i];
-    const float ids = id[i];
-    const float nx = nrm[3 * i], ny = nrm[3 * i + 1], nz = nrm[3 * i + 2];
+// The lanes of one warp draw surfel i: they sweep the pixel box around its disc of radius r.  Eq. 3
+// is taken in the tile-local form id_u = id_s (1 + ((r_u - r_s) . n) / (r_s . n)), which has no
+// cancellation for pixels near the surfel's centre.
+__device__ __forceinline__ void draw_surfel(const Cam& cam, int W, int H, float2 us, float ids, float nx, float ny,
+                                            float nz, float radius, int i, int lane, unsigned long long* zbuf) {
     const float rsx = (us.x - cam.cx) * cam.ifx, rsy = (us.y - cam.cy) * cam.ify;
     const float rsn = fmaf(rsx, nx, fmaf(rsy, ny, nz));
     const float inv_rsn = 1.0f / rsn;
@@ -137,6 +130,30 @@ __global__ void __launch_bounds__(256) k_render_surfels(const Cam cam, int W, in
         const unsigned long long key = (static_cast<unsigned long long>(__float_as_uint(v)) << 32) | lo;
         atomicMax(zbuf + size_t(y) * W + x, key);
     }
+}
+
+// One warp per free surfel.
+__global__ void __launch_bounds__(256) k_render_surfels(const Cam cam, int W, int H, int n, const float2* __restrict__ u,
+                                                        const float* __restrict__ id, const float* __restrict__ nrm,
+                                                        const uint8_t* __restrict__ valid, float radius,
+                                                        unsigned long long* __restrict__ zbuf) {
+    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (i >= n || !valid[i]) return;
+    draw_surfel(cam, W, H, u[i], id[i], nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2], radius, i, lane, zbuf);
+}
+
+// One warp per surfel of a plan with circular surfels: centre = tile centre, drawn unless EMPTY or
+// UNSEEDED.  The same draw as k_render_surfels, so the map equals the render of the plan's surfels
+// as free surfels.
+__global__ void __launch_bounds__(256) k_render_plan_discs(const Cam cam, const __grid_constant__ sgn::PlanParams pp) {
+    const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (s >= pp.S) return;
+    const int st = pp.status[s] & 0x3f;
+    if (st == SGN_SURFEL_EMPTY || st == SGN_SURFEL_UNSEEDED) return;
+    const float half = 0.5f * float(pp.P - 1);
+    const float2 us = make_float2(float((s % pp.TX) * pp.P) + half, float((s / pp.TX) * pp.P) + half);
+    draw_surfel(cam, pp.W, pp.H, us, pp.id[s], pp.n[3 * s], pp.n[3 * s + 1], pp.n[3 * s + 2], pp.radius, s, lane,
+                pp.zbuf);
 }
 
 __global__ void __launch_bounds__(256) k_resolve_depth(int npx, const unsigned long long* __restrict__ zbuf,
@@ -206,3 +223,37 @@ extern "C" sgn_status sgn_render_surfels(const double intrinsics[4], int width, 
     sgn::count_launch(n > 0 ? 2 : 1);
     return SGN_OK;
 }
+
+namespace sgn {
+
+int disc_pixels(int P, float radius, int* out_xy) {
+    const double c = 0.5 * (P - 1), r = double(radius);
+    const int lo = int(std::floor(c - r)) - 1, hi = int(std::ceil(c + r)) + 1;
+    int n = 0;
+    for (int y = lo; y <= hi; ++y)
+        for (int x = lo; x <= hi; ++x) {
+            const double dx = x - c, dy = y - c;
+            if (!(std::sqrt(dx * dx + dy * dy) < r)) continue;
+            if (n == kMaxDiscPixels) return -1;
+            if (out_xy) {
+                out_xy[2 * n] = x;
+                out_xy[2 * n + 1] = y;
+            }
+            ++n;
+        }
+    return n;
+}
+
+int launch_render_discs(const PlanParams& pp, void* stream) {
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t npx = size_t(pp.W) * pp.H;
+    cudaError_t e = cudaMemsetAsync(pp.zbuf, 0, npx * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return int(e);
+    const Cam cam{pp.fx, pp.fy, pp.cx, pp.cy, pp.ifx, pp.ify};
+    if (pp.S > 0) k_render_plan_discs<<<(pp.S + 7) / 8, 256, 0, st>>>(cam, pp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return int(e);
+    k_resolve_depth<<<int((npx + 255) / 256), 256, 0, st>>>(int(npx), pp.zbuf, pp.depth, pp.sidx);
+    return int(cudaGetLastError());
+}
+
+}  // namespace sgn

@@ -65,6 +65,40 @@ __global__ void __launch_bounds__(256, gn_min_blocks(P, G))
     gn_surfel<P, G, DT, true>(&spp, gtid / G, lg, iters, mode, scratch, &st);
 }
 
+// Circular surfels: one warp per surfel, DPPL disc pixels per lane in passes of four.
+template <int P, int DT, int DPPL>
+__global__ void __launch_bounds__(256, 2) k_gn_disc(const __grid_constant__ PlanParams pp, int iters, int mode) {
+    __shared__ PlanParams spp;
+    extern __shared__ float4 sdyn[];
+    load_plan(&spp, &pp);
+    __syncthreads();
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    float* scratch = reinterpret_cast<float*>(sdyn) + (threadIdx.x / 32) * group_scratch_words(pp.F);
+    gn_surfel<P, 32, DT, false, 4, DPPL>(&spp, gtid / 32, threadIdx.x % 32, iters, mode, scratch);
+}
+
+template <int P, int DT, int DPPL>
+int launch_disc(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st) {
+    static bool attr_set = false;  // same value from every thread: a benign race
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(k_gn_disc<P, DT, DPPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   scratch_bytes(8, kMaxFrames));
+        if (e != cudaSuccess) return int(e);
+        attr_set = true;
+    }
+    k_gn_disc<P, DT, DPPL><<<grid, block, scratch_bytes(block / 32, pp.F), st>>>(pp, iters, mode);
+    return int(cudaGetLastError());
+}
+
+template <int P, int DT>
+int launch_disc_ppl(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st) {
+    if (pp.disc_n <= 2 * 32) return launch_disc<P, DT, 2>(pp, iters, mode, grid, block, st);
+    if (pp.disc_n <= 4 * 32) return launch_disc<P, DT, 4>(pp, iters, mode, grid, block, st);
+    if (pp.disc_n <= 8 * 32) return launch_disc<P, DT, 8>(pp, iters, mode, grid, block, st);
+    if (pp.disc_n <= 16 * 32) return launch_disc<P, DT, 16>(pp, iters, mode, grid, block, st);
+    return int(cudaErrorInvalidConfiguration);
+}
+
 template <int P, int G, int DT>
 int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st, const void* tmap) {
     const int scratch = scratch_bytes(block / G, pp.F);
@@ -101,6 +135,15 @@ int launch_gn_dtype(const PlanParams& pp, int iters, int mode, int G, int block,
     const int grid = int((threads + block - 1) / block);
     if (grid == 0) return cudaSuccess;
     if (block > 256 || block % G) return int(cudaErrorInvalidConfiguration);
+    if (pp.disc_n > 0) {  // circular surfels: 32 lanes per surfel, no staging
+        if (G != 32) return int(cudaErrorInvalidConfiguration);
+        switch (pp.P) {
+            case 4: return launch_disc_ppl<4, DT>(pp, iters, mode, grid, block, st);
+            case 8: return launch_disc_ppl<8, DT>(pp, iters, mode, grid, block, st);
+            case 16: return launch_disc_ppl<16, DT>(pp, iters, mode, grid, block, st);
+            default: return int(cudaErrorInvalidConfiguration);
+        }
+    }
 #define SGN_GN_CASE(PP, GG) \
     if (pp.P == PP && G == GG) return launch_one<PP, GG, DT>(pp, iters, mode, grid, block, st, tmap);
     SGN_GN_CASE(4, 8)

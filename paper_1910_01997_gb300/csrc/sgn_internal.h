@@ -75,6 +75,12 @@ struct PlanParams {
     float* depth;               // W x H, tightly packed
     int32_t* sidx;
     unsigned int* stage_err;    // device counter of staging waits that timed out (library-wide)
+    // circular surfels (radius > 0): the disc's pixels as (x, y) offsets from the tile origin,
+    // disc_n pairs; a depth buffer of W x H keys for the render of the discs
+    float radius;
+    int disc_n;
+    const int* disc;
+    unsigned long long* zbuf;
     FramePose frames[kMaxFrames];
 };
 
@@ -91,6 +97,15 @@ SGN_HD constexpr int box_bytes(int P, int dtype) { return box_w(P, dtype) * box_
 SGN_HD constexpr int box_stride(int P, int dtype) { return (box_bytes(P, dtype) + 127) / 128 * 128; }
 constexpr int kStageSlots = 2;  // boxes in flight per surfel (double buffering)
 constexpr int kTensorMapBytes = 128;
+
+// Circular surfels: at most this many pixels per disc (radius up to about 12.7).
+constexpr int kMaxDiscPixels = 512;
+// Pixels (x, y offsets from the tile origin, row-major) strictly within `radius` of the tile centre
+// ((P - 1) / 2, (P - 1) / 2) (Eq. 4); returns the count (or -1 when more than kMaxDiscPixels).
+int disc_pixels(int P, float radius, int* out_xy);
+// Depth-buffered render of a plan's circular surfels (tile centres, status not EMPTY/UNSEEDED) into
+// pp.depth / pp.sidx using pp.zbuf.  Returns cudaError_t cast to int.
+int launch_render_discs(const PlanParams& pp, void* stream);
 
 // Encodes the TMA descriptor of a plan's texel planes (planes frames of H rows, 4 components per
 // texel) with the staging box of patch P into tmap (kTensorMapBytes, 64-byte aligned host memory).

@@ -98,7 +98,7 @@ extern "C" sgn_status sgn_solve_static(const sgn_plan_desc* d, const double intr
         return error(SGN_ERR_INVALID_ARGUMENT, "unknown image dtype");
     if (!(d->huber_k > 0.0f) || !std::isfinite(d->huber_k) || !(d->lm_lambda >= 0.0f) || !std::isfinite(d->lm_lambda) ||
         std::isnan(d->fp64_cond) || (d->optimize_normal != 0 && d->optimize_normal != 1) || d->min_residuals < 0 ||
-        (d->lm_adaptive != 0 && d->lm_adaptive != 1))
+        (d->lm_adaptive != 0 && d->lm_adaptive != 1) || d->surfel_radius != 0.0f)
         return error(SGN_ERR_INVALID_ARGUMENT, "invalid solver options in desc");
     if (num_frames < 1 || num_frames > SGN_MAX_FRAMES) return error(SGN_ERR_INVALID_ARGUMENT, "num_frames outside [1, %d]", SGN_MAX_FRAMES);
     if (iters < 0 || iters > 100000) return error(SGN_ERR_INVALID_ARGUMENT, "iters outside [0, 100000]");
@@ -160,6 +160,7 @@ extern "C" sgn_status sgn_solve_static(const sgn_plan_desc* d, const double intr
     pp.optimize_normal = d->optimize_normal;
     pp.min_residuals = d->min_residuals;
     pp.lm_adaptive = d->lm_adaptive;
+    pp.radius = 0.0f;  // tiles only: circular surfels need a pixel table and a depth buffer
     pp.kf = keyframe;
     pp.kf_pitch = int(keyframe_pitch_bytes / 4);
     pp.tex = scratch;
