@@ -87,7 +87,8 @@ typedef struct {
                                  lm_lambda: a step is kept when the mean Huber cost over valid samples
                                  decreases (lambda / 10), otherwise dropped (lambda x 10); a singular system
                                  or an unusable step counts as dropped; lambda stays in [1e-7, 1e7]; one
-                                 extra cost evaluation per solve */
+                                 extra cost evaluation per solve.  Such plans are solved per plan (not in
+                                 a batch or a server), without texel staging, with square surfels */
     float surfel_radius;      /* 0 (default): surfel s is its P x P tile.  In [0.5, 16]: surfel s is the set
                                  of pixels whose centre lies strictly within this radius of its tile centre
                                  (the paper's circular surfel, Eq. 4; at most 512 pixels); discs of

@@ -332,6 +332,8 @@ sgn_status sgn_plan_create(const sgn_plan_desc* d, sgn_plan** out) {
     if (d->min_residuals < 0) return fail(SGN_ERR_INVALID_ARGUMENT, "min_residuals must be >= 0");
     if (d->lm_adaptive != 0 && d->lm_adaptive != 1) return fail(SGN_ERR_INVALID_ARGUMENT, "lm_adaptive must be 0 or 1");
     std::vector<int> disc;
+    if (d->surfel_radius != 0.0f && d->lm_adaptive)
+        return fail(SGN_ERR_INVALID_ARGUMENT, "circular surfels use the fixed damping (lm_adaptive = 0)");
     if (d->surfel_radius != 0.0f) {
         if (!(d->surfel_radius >= 0.5f) || !(d->surfel_radius <= 16.0f))
             return fail(SGN_ERR_INVALID_ARGUMENT, "surfel_radius must be 0 (tiles) or in [0.5, 16]");
@@ -756,6 +758,7 @@ sgn_status sgn_batch_add(sgn_batch* b, sgn_plan* p) {
     if (!b || !p) return fail(SGN_ERR_INVALID_ARGUMENT, "batch/plan is NULL");
     if (int(b->plans.size()) >= b->max_plans) return fail(SGN_ERR_INVALID_ARGUMENT, "batch is full (%d plans)", b->max_plans);
     if (!p->disc.empty()) return fail(SGN_ERR_INVALID_ARGUMENT, "circular surfels are solved per plan, not in a batch");
+    if (p->desc.lm_adaptive) return fail(SGN_ERR_INVALID_ARGUMENT, "the Marquardt schedule is solved per plan, not in a batch");
     b->plans.push_back(p);
     b->dirty = true;
     return SGN_OK;

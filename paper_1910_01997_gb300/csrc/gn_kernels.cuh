@@ -25,7 +25,7 @@ constexpr int gn_min_blocks(int P, int G) { return P * P / G <= 2 ? 3 : (P * P /
 // 16-byte aligned), then, when staging, each group's texel boxes (128-byte aligned).
 __host__ __device__ constexpr int scratch_bytes(int groups, int F) { return groups * group_scratch_words(F) * 4; }
 
-template <int P, int G, int DT>
+template <int P, int G, int DT, bool LMA = false>
 __global__ void __launch_bounds__(256, gn_min_blocks(P, G)) k_gn(const __grid_constant__ PlanParams pp, int iters, int mode) {
     __shared__ PlanParams spp;
     extern __shared__ float4 sdyn[];
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256, gn_min_blocks(P, G)) k_gn(const __grid_co
     __syncthreads();
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     float* scratch = reinterpret_cast<float*>(sdyn) + (threadIdx.x / G) * group_scratch_words(pp.F);
-    gn_surfel<P, G, DT>(&spp, gtid / G, threadIdx.x % G, iters, mode, scratch);
+    gn_surfel<P, G, DT, false, 8, 0, LMA>(&spp, gtid / G, threadIdx.x % G, iters, mode, scratch);
 }
 
 // Staged variant: every group of G lanes also owns kStageSlots texel boxes (box_stride(P, DT) bytes
@@ -102,8 +102,19 @@ int launch_disc_ppl(const PlanParams& pp, int iters, int mode, int grid, int blo
 template <int P, int G, int DT>
 int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st, const void* tmap) {
     const int scratch = scratch_bytes(block / G, pp.F);
-    if (!tmap) {
+    if (pp.lm_adaptive) {  // Marquardt schedule: its own instantiation (direct gathers)
         static bool attr_set = false;  // same value from every thread: a benign race
+        if (!attr_set) {
+            const cudaError_t e = cudaFuncSetAttribute(k_gn<P, G, DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       scratch_bytes(256 / G, kMaxFrames));
+            if (e != cudaSuccess) return int(e);
+            attr_set = true;
+        }
+        k_gn<P, G, DT, true><<<grid, block, scratch, st>>>(pp, iters, mode);
+        return int(cudaGetLastError());
+    }
+    if (!tmap) {
+        static bool attr_set = false;
         if (!attr_set) {
             const cudaError_t e = cudaFuncSetAttribute(k_gn<P, G, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        scratch_bytes(256 / G, kMaxFrames));

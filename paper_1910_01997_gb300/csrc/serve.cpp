@@ -439,7 +439,8 @@ sgn_status sgn_server_create(void* d_arena, size_t arena_bytes, int max_slots, i
 sgn_status sgn_server_submit(sgn_server* s, const sgn_request* r) {
     if (!s || !r) return srv_error(SGN_ERR_INVALID_ARGUMENT, "server: NULL argument");
     const sgn_plan_desc& d = r->desc;
-    if (d.surfel_radius != 0.0f) return srv_error(SGN_ERR_INVALID_ARGUMENT, "server: circular surfels are not served");
+    if (d.surfel_radius != 0.0f || d.lm_adaptive)
+        return srv_error(SGN_ERR_INVALID_ARGUMENT, "server: requests use square surfels and the fixed damping");
     sgn_plan* probe = nullptr;
     sgn_status st = sgn_plan_create(&d, &probe);  // validates the description
     if (st != SGN_OK) return st;
