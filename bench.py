@@ -46,6 +46,56 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+class Ranks:
+    """The N-replica timing protocol.  Each rank solves its own keyframes (no collective on the data
+    path); the ranks meet at a barrier on both sides of a timed region, the region's time is the
+    slowest rank's, the throughput counts the units all ranks processed in that time, and rank 0
+    alone prints.  With one rank every call is local."""
+
+    def __init__(self, backend: str = "nccl"):
+        self.rank, self.world, self.local = dist_env()
+        self.dist = None
+        self.device = "cpu"
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group(backend)
+            self.dist = dist
+            if backend == "nccl":
+                self.device = f"cuda:{self.local}"
+
+    @property
+    def root(self) -> bool:
+        return self.rank == 0
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max_ms(self, ms: float) -> float:
+        """The largest of the ranks' times."""
+        if self.dist is None:
+            return float(ms)
+        import torch
+
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def throughput(self, units_per_rank: float, ms: float) -> float:
+        """Units all ranks processed per second, over the slowest rank's time."""
+        return self.world * units_per_rank / (ms / 1e3)
+
+    def report(self, line: dict, out=None):
+        if self.root:
+            print(json.dumps(line), file=out or sys.stdout, flush=True)
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 def make_problem(rank: int):
     import synth
 
@@ -423,12 +473,9 @@ def run_ours(args):
 
     import paper_1910_01997_gb300 as sgn
 
-    rank, world, local = dist_env()
+    ranks = Ranks("nccl")
+    rank, world, local = ranks.rank, ranks.world, ranks.local
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
     prob = make_problem(rank)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
@@ -489,8 +536,7 @@ def run_ours(args):
         plan._keep.clear()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        if world > 1:
-            torch.distributed.barrier()
+        ranks.barrier()
         torch.cuda.synchronize()
         with ClockSampler(local) as clocks:
             time.sleep(0.3)
@@ -507,15 +553,10 @@ def run_ours(args):
             stream.synchronize()
         launches = launches_per_step * args.steps
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        ranks.barrier()
         step_ms = [e[0].elapsed_time(e[1]) for e in ev]
         kern_ms = [e[2].elapsed_time(e[3]) for e in ev]
-        total_ms = sum(step_ms)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = ranks.max_ms(sum(step_ms))
 
         # end to end through the C ABI from page-locked host buffers
         h_kf = torch.from_numpy(prob.keyframe).pin_memory()
@@ -542,22 +583,21 @@ def run_ours(args):
             flush.zero_()
             e2e_step()
         e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        ranks.barrier()
         for i in range(args.steps):
             flush.zero_()
             e2e_ev[i][0].record(stream)
             e2e_step()
             e2e_ev[i][1].record(stream)
         torch.cuda.synchronize()
-        e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        ranks.barrier()
+        e2e_ms = ranks.max_ms(sum(a.elapsed_time(b) for a, b in e2e_ev))
     h2d = prob.keyframe.nbytes + prob.frames.nbytes + S * (4 + 12 + 1)
     d2h = S * (4 + 12 + 4 + 4 + 1) + W * H * 8
 
     res = residuals_per_step(prob)
-    value = world * res * args.steps / (total_ms / 1e3)
+    value = ranks.throughput(res * args.steps, total_ms)
     peak, peak_kind = measured_peaks()
     kern_avg_s = statistics.mean(kern_ms) / 1e3
     achieved = res * BYTES_PER_RESIDUAL[WORKLOAD["texels"]] / kern_avg_s / 1e9
@@ -574,7 +614,7 @@ def run_ours(args):
                      "traffic": profiled_traffic(), "kernel": "k_gn<8,16,f32>",
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "note": "algorithmic bytes = residuals x 12 B (I, gx, gy in FP32) per launch / CUDA-event launch time"},
-        "e2e": {"value": world * res * args.steps / (e2e_ms / 1e3), "unit": "residuals/s",
+        "e2e": {"value": ranks.throughput(res * args.steps, e2e_ms), "unit": "residuals/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "step_graphs": "uploads+prep, solve, readback: 3 CUDA graph replays per step",
@@ -589,13 +629,12 @@ def run_ours(args):
         line["serving"] = serving_leg(args.serve_seconds, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    ranks.report(line)
+    ranks.close()
 
 
 def run_reference(args):
+    """The oracle on the host cores; under N ranks rank 0 alone runs it and the others exit at once."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
