@@ -107,3 +107,46 @@ def test_batch_host_side_checks(sgn):
         sgn.sgn_batch_set_schedule(b, 2, 64)
     sgn.sgn_batch_destroy(b)
     sgn.sgn_plan_destroy(h)
+
+
+def test_circular_surfel_desc_validation(sgn):
+    d = sgn.sgn_plan_desc_default(128, 96, 8, 3)
+    d.surfel_radius = 8 / 3.5449077  # area of the 8x8 tile
+    h = sgn.sgn_plan_create(d)
+    sgn.sgn_plan_destroy(h)
+    for radius, adaptive in ((-1.0, 0), (0.3, 0), (16.5, 0), (float("nan"), 0), (13.0, 0), (4.0, 1)):
+        d = sgn.sgn_plan_desc_default(128, 96, 8, 3)
+        d.surfel_radius, d.lm_adaptive = radius, adaptive
+        with pytest.raises(sgn.SgnError) as e:
+            sgn.sgn_plan_create(d)
+        assert e.value.status == sgn.SGN_ERR_INVALID_ARGUMENT, (radius, adaptive)
+
+
+def test_transfer_and_render_argument_checks(sgn):
+    """Host-side checks of the frame-change and render calls, taken before any device work."""
+    lib = ctypes.CDLL(sgn.LIB_PATH)
+    D4, D12 = ctypes.c_double * 4, ctypes.c_double * 12
+    cam, bad_cam = D4(140.0, 140.0, 79.5, 59.5), D4(-1.0, 140.0, 79.5, 59.5)
+    rigid = D12(1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0)
+    scaled = D12(2, 0, 0, 0, 0, 2, 0, 0, 0, 0, 2, 0)
+    host = (ctypes.c_float * 16)()
+    p = ctypes.cast(host, ctypes.c_void_p)
+    transfer = lambda c, T, n, ptr: sgn._status("sgn_transfer_surfels", c, T, n, ptr, ptr, ptr, ptr, ptr, ptr, ptr, None)
+    assert transfer(bad_cam, rigid, 1, p) == sgn.SGN_ERR_INVALID_ARGUMENT
+    assert transfer(cam, scaled, 1, p) == sgn.SGN_ERR_INVALID_ARGUMENT
+    assert transfer(cam, rigid, -1, p) == sgn.SGN_ERR_INVALID_ARGUMENT
+    assert transfer(cam, rigid, 0, None) == sgn.SGN_OK  # nothing to move
+    assert transfer(cam, rigid, 2, p) == sgn.SGN_ERR_INVALID_ARGUMENT  # host memory
+    assert "device memory" in sgn.sgn_last_error()
+
+    def render(c, W, H, n, radius, ptr):
+        return sgn._status("sgn_render_surfels", c, W, H, n, ptr, ptr, ptr, ptr, radius, ptr, ptr, ptr, None)
+
+    assert render(bad_cam, 160, 120, 1, 3.0, p) == sgn.SGN_ERR_INVALID_ARGUMENT
+    for W, H in ((0, 120), (160, 0), (16385, 120)):
+        assert render(cam, W, H, 1, 3.0, p) == sgn.SGN_ERR_INVALID_ARGUMENT
+    assert render(cam, 160, 120, -1, 3.0, p) == sgn.SGN_ERR_INVALID_ARGUMENT
+    for radius in (0.0, -2.0, float("nan"), 2000.0):
+        assert render(cam, 160, 120, 1, radius, p) == sgn.SGN_ERR_INVALID_ARGUMENT
+    assert render(cam, 160, 120, 1, 3.0, p) == sgn.SGN_ERR_INVALID_ARGUMENT  # host memory
+    assert lib.sgn_abi_version() == 2
