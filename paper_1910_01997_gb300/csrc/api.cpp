@@ -273,6 +273,44 @@ sgn_status require_ready(const sgn_plan* p) {
 cudaMemcpyKind kind_to_device(sgn_mem m) { return m == SGN_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
 cudaMemcpyKind kind_from_device(sgn_mem m) { return m == SGN_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
 
+// A call's stream-ordered transfers: device-side ones go out as one copy kernel (a single graph
+// node instead of one memcpy node per range), host-side ones, or any range the device cannot
+// address directly, as one cudaMemcpy(2D)Async each.
+struct Transfers {
+    sgn::CopyJob job[sgn::kMaxCopyJobs];
+    int n = 0;
+    void add(void* dst, const void* src, size_t bytes) { add_rows(dst, bytes, src, bytes, bytes, 1); }
+    void add_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes, int rows) {
+        if (row_bytes == 0 || rows <= 0) return;
+        job[n++] = sgn::CopyJob{dst, src, dpitch, spitch, row_bytes, rows};
+    }
+    static bool device_accessible(const void* q) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
+               (a.type == cudaMemoryTypeHost && a.devicePointer == q);
+    }
+    cudaError_t issue(sgn_mem mem, cudaMemcpyKind kind, cudaStream_t st) const {
+        bool kernel = mem == SGN_DEVICE;
+        for (int i = 0; kernel && i < n; ++i) kernel = device_accessible(job[i].dst) && device_accessible(job[i].src);
+        if (kernel) {
+            const int e = sgn::launch_copy_jobs(job, n, st);
+            if (e == cudaSuccess && n > 0) sgn::count_launch();
+            return cudaError_t(e);
+        }
+        for (int i = 0; i < n; ++i) {
+            const sgn::CopyJob& j = job[i];
+            const cudaError_t e = j.rows == 1 ? cudaMemcpyAsync(j.dst, j.src, j.row_bytes, kind, st)
+                                              : cudaMemcpy2DAsync(j.dst, j.dpitch, j.src, j.spitch, j.row_bytes, j.rows, kind, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+};
+
 sgn_status sync_event(cudaEvent_t ev, cudaStream_t stream, uint64_t timeout_ns) {
     cudaError_t e = cudaEventRecord(ev, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
@@ -471,8 +509,9 @@ sgn_status sgn_set_keyframe(sgn_plan* p, const float* img, size_t pitch, sgn_mem
     if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
     if (pitch < size_t(W) * sizeof(float) || pitch % sizeof(float)) return fail(SGN_ERR_INVALID_ARGUMENT, "keyframe pitch %zu invalid for width %d", pitch, W);
     DeviceGuard g(p->device);
-    cudaError_t e = cudaMemcpy2DAsync(p->ws + p->L.kf, size_t(p->L.kf_pitch) * sizeof(float), img, pitch,
-                                      size_t(W) * sizeof(float), H, kind_to_device(mem), p->stream);
+    Transfers t;
+    t.add_rows(p->ws + p->L.kf, size_t(p->L.kf_pitch) * sizeof(float), img, pitch, size_t(W) * sizeof(float), H);
+    const cudaError_t e = t.issue(mem, kind_to_device(mem), p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "keyframe upload");
     p->kf_set = true;
     return SGN_OK;
@@ -574,10 +613,11 @@ sgn_status sgn_init_surfels(sgn_plan* p, const float* id, const float* n, const 
         }
     }
     DeviceGuard g(p->device);
-    const cudaMemcpyKind k = kind_to_device(mem);
-    cudaError_t e = cudaMemcpyAsync(p->ws + p->L.id0, id, S * sizeof(float), k, p->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.n0, n, 3 * S * sizeof(float), k, p->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->ws + p->L.state0, state, S, k, p->stream);
+    Transfers t;
+    t.add(p->ws + p->L.id0, id, S * sizeof(float));
+    t.add(p->ws + p->L.n0, n, 3 * S * sizeof(float));
+    t.add(p->ws + p->L.state0, state, S);
+    const cudaError_t e = t.issue(mem, kind_to_device(mem), p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "surfel upload");
     // The working state is derived from the initial surfels on first need (sgn_solve rebuilds it
     // itself, so a solve right after the upload launches nothing extra).
@@ -649,13 +689,13 @@ sgn_status sgn_read_surfels(sgn_plan* p, float* id, float* n, float* cost, int32
     DeviceGuard g(p->device);
     if ((st = ensure_state(p)) != SGN_OK) return st;
     const size_t S = size_t(p->S);
-    const cudaMemcpyKind k = kind_from_device(mem);
-    cudaError_t e = cudaSuccess;
-    if (id && e == cudaSuccess) e = cudaMemcpyAsync(id, p->ws + p->L.id, S * sizeof(float), k, p->stream);
-    if (n && e == cudaSuccess) e = cudaMemcpyAsync(n, p->ws + p->L.n, 3 * S * sizeof(float), k, p->stream);
-    if (cost && e == cudaSuccess) e = cudaMemcpyAsync(cost, p->ws + p->L.cost, S * sizeof(float), k, p->stream);
-    if (nres && e == cudaSuccess) e = cudaMemcpyAsync(nres, p->ws + p->L.nres, S * sizeof(int32_t), k, p->stream);
-    if (status && e == cudaSuccess) e = cudaMemcpyAsync(status, p->ws + p->L.status, S, k, p->stream);
+    Transfers t;
+    if (id) t.add(id, p->ws + p->L.id, S * sizeof(float));
+    if (n) t.add(n, p->ws + p->L.n, 3 * S * sizeof(float));
+    if (cost) t.add(cost, p->ws + p->L.cost, S * sizeof(float));
+    if (nres) t.add(nres, p->ws + p->L.nres, S * sizeof(int32_t));
+    if (status) t.add(status, p->ws + p->L.status, S);
+    const cudaError_t e = t.issue(mem, kind_from_device(mem), p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "surfel readback");
     return SGN_OK;
 }
@@ -675,10 +715,10 @@ sgn_status sgn_read_depth_map(sgn_plan* p, float* inv_depth, int32_t* sidx, sgn_
         p->depth_valid = true;
     }
     const size_t npx = size_t(p->desc.width) * p->desc.height;
-    const cudaMemcpyKind k = kind_from_device(mem);
-    cudaError_t e = cudaSuccess;
-    if (inv_depth) e = cudaMemcpyAsync(inv_depth, p->ws + p->L.depth, npx * sizeof(float), k, p->stream);
-    if (sidx && e == cudaSuccess) e = cudaMemcpyAsync(sidx, p->ws + p->L.sidx, npx * sizeof(int32_t), k, p->stream);
+    Transfers t;
+    if (inv_depth) t.add(inv_depth, p->ws + p->L.depth, npx * sizeof(float));
+    if (sidx) t.add(sidx, p->ws + p->L.sidx, npx * sizeof(int32_t));
+    const cudaError_t e = t.issue(mem, kind_from_device(mem), p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "depth map readback");
     return SGN_OK;
 }

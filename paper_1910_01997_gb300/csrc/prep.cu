@@ -1,5 +1,6 @@
 // Frame preparation, surfel initialisation/seeding and depth-map rendering kernels, and the
 // dtype dispatch of the Gauss-Newton launcher.
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda.h>
@@ -143,6 +144,56 @@ int launch_prep_frames(const PlanParams& pp, const float* const* src, const size
     a.dtype = pp.dtype;
     dim3 block(32, 8), grid((pp.W + 31) / 32, (pp.H + 7) / 8, count);
     k_prep_frames<<<grid, block, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    return int(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------------------ device copies
+
+struct CopyArgs {
+    CopyJob job[kMaxCopyJobs];
+    int n;
+};
+
+// blockIdx.z: job; blockIdx.y: rows (grid-stride); x: the row's 16-byte words (grid-stride), or its
+// 4-byte words / bytes when the job's addresses and pitches do not allow wider accesses.
+__global__ void __launch_bounds__(256) k_copy_jobs(const __grid_constant__ CopyArgs a) {
+    const CopyJob& j = a.job[blockIdx.z];
+    const uintptr_t al = reinterpret_cast<uintptr_t>(j.dst) | reinterpret_cast<uintptr_t>(j.src) | j.dpitch | j.spitch;
+    const size_t x0 = size_t(blockIdx.x) * blockDim.x + threadIdx.x, xs = size_t(gridDim.x) * blockDim.x;
+    for (int r = blockIdx.y; r < j.rows; r += gridDim.y) {
+        char* d = static_cast<char*>(j.dst) + size_t(r) * j.dpitch;
+        const char* s = static_cast<const char*>(j.src) + size_t(r) * j.spitch;
+        size_t done = 0;
+        if ((al & 15) == 0) {
+            const size_t n16 = j.row_bytes / 16;
+            for (size_t i = x0; i < n16; i += xs)
+                reinterpret_cast<uint4*>(d)[i] = __ldg(reinterpret_cast<const uint4*>(s) + i);
+            done = n16 * 16;
+        } else if ((al & 3) == 0) {
+            const size_t n4 = j.row_bytes / 4;
+            for (size_t i = x0; i < n4; i += xs)
+                reinterpret_cast<unsigned*>(d)[i] = __ldg(reinterpret_cast<const unsigned*>(s) + i);
+            done = n4 * 4;
+        }
+        for (size_t i = done + x0; i < j.row_bytes; i += xs) d[i] = s[i];
+    }
+}
+
+int launch_copy_jobs(const CopyJob* jobs, int n, void* stream) {
+    if (n <= 0) return cudaSuccess;
+    if (n > kMaxCopyJobs) return cudaErrorInvalidValue;
+    CopyArgs a{};
+    size_t widest = 1;
+    int rows = 1;
+    for (int i = 0; i < n; ++i) {
+        a.job[i] = jobs[i];
+        widest = std::max(widest, (jobs[i].row_bytes + 15) / 16);
+        rows = std::max(rows, jobs[i].rows);
+    }
+    a.n = n;
+    const unsigned gx = unsigned(std::min<size_t>((widest + 255) / 256, 1024));
+    const unsigned gy = unsigned(std::min(rows, 4096));
+    k_copy_jobs<<<dim3(gx, gy, n), 256, 0, static_cast<cudaStream_t>(stream)>>>(a);
     return int(cudaGetLastError());
 }
 

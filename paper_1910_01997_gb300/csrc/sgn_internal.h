@@ -130,6 +130,18 @@ int launch_prep_frames(const PlanParams& pp, const float* const* src, const size
 int launch_gn(const PlanParams& pp, int iters, int mode, int lanes_per_surfel, int block_threads, void* stream,
               const void* tmap = nullptr);
 int launch_seed(const PlanParams& pp, void* stream);
+
+// Device-side copies (stream-ordered like cudaMemcpyAsync, but up to kMaxCopyJobs ranges in one
+// kernel launch): job j copies `rows` rows of `row_bytes` bytes from src (row stride spitch bytes)
+// to dst (row stride dpitch bytes).  Both sides must be device-accessible.
+struct CopyJob {
+    void* dst;
+    const void* src;
+    size_t dpitch, spitch, row_bytes;
+    int rows;
+};
+constexpr int kMaxCopyJobs = 8;
+int launch_copy_jobs(const CopyJob* jobs, int n, void* stream);
 int launch_init_state(const PlanParams& pp, void* stream);
 int launch_render_depth(const PlanParams& pp, void* stream);
 
