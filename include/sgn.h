@@ -42,7 +42,7 @@ extern "C" {
 #endif
 
 #define SGN_MAX_FRAMES 16
-#define SGN_ABI_VERSION 2
+#define SGN_ABI_VERSION 3
 
 typedef enum {
     SGN_OK = 0,
@@ -360,13 +360,17 @@ sgn_status sgn_staging_timeouts(uint32_t* count);
 
 /* ---- introspection --------------------------------------------------------------------- */
 
-/* Diagnostic (no counterpart in the paper): r[i] = 1 / x[i] for n values, computed exactly as the
- * FP64 normal-equation solve computes its pivot reciprocals (hardware estimate plus a series
- * correction), so that tests can compare it with IEEE division.  x and r are device pointers to n
- * doubles (they may alias); every x[i] must be a positive normal double.  Enqueued on `stream`
- * (cudaStream_t, may be NULL); n = 0 is a no-op; NULL pointers with n > 0 or n < 0 give
+/* Diagnostic: the FP64 route of the damped normal-equation solve of Sec. 2.4 (the step of Eq. 7
+ * with Levenberg-Marquardt damping), run on n given systems exactly as the Gauss-Newton kernels run
+ * it (Cramer's rule, one component per lane of a 16-lane group): (H + lambda diag(m, m, H33)) delta
+ * = -g, m = (H11 + H22) / 2.  H6: n x 6 floats, the upper triangle (H11, H12, H13, H22, H23, H33)
+ * row by row; g3: n x 3 floats; delta: n x 3 floats out; pd: n int32 out, 1 when the damped matrix
+ * is positive definite (its leading principal minors are positive in FP64), else 0 (delta is then
+ * meaningless).  All arrays are device pointers; enqueued on `stream` (cudaStream_t, may be NULL);
+ * n = 0 is a no-op; NULL arrays with n > 0, n < 0 or lambda not >= 0 give
  * SGN_ERR_INVALID_ARGUMENT. */
-sgn_status sgn_check_fp64_reciprocal(const double* x, double* r, int n, void* stream);
+sgn_status sgn_check_fp64_solve(const float* H6, const float* g3, double lambda, int n, float* delta, int32_t* pd,
+                                void* stream);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char* sgn_last_error(void);

@@ -117,7 +117,7 @@ _SIGS = {
     "sgn_batch_run": [_P, _I],
     "sgn_batch_sync": [_P, ctypes.c_uint64],
     "sgn_batch_destroy": [_P],
-    "sgn_check_fp64_reciprocal": [_P, _P, _I, _P],
+    "sgn_check_fp64_solve": [_P, _P, ctypes.c_double, _I, _P, _P, _P],
     "sgn_plan_set_staging": [_P, _I],
     "sgn_transfer_surfels": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _I, _P, _P, _P, _P, _P,
                              _P, _P, _P],
@@ -422,17 +422,19 @@ def sgn_staging_timeouts() -> int:
     return int(n.value)
 
 
-def sgn_check_fp64_reciprocal(x, stream=None):
-    """Reciprocals of the positive FP64 CUDA tensor x as the FP64 solve computes them (diagnostic)."""
+def sgn_check_fp64_solve(H6, g3, lam, stream=None):
+    """The FP64 route of the damped solve on the systems of the float32 CUDA tensors H6 (n, 6) and
+    g3 (n, 3) (diagnostic).  Returns (delta (n, 3) float32, positive definite (n,) bool) on the GPU."""
     import torch
 
-    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
-        raise ValueError("x must be a contiguous float64 CUDA tensor")
-    r = torch.empty_like(x)
+    n = int(H6.shape[0]) if isinstance(H6, torch.Tensor) and H6.dim() == 2 else -1
+    delta = torch.empty(max(n, 0), 3, device=H6.device)
+    pd = torch.empty(max(n, 0), dtype=torch.int32, device=H6.device)
     s = torch.cuda.current_stream() if stream is None else stream
-    _call("sgn_check_fp64_reciprocal", x.data_ptr(), r.data_ptr(), x.numel(), s.cuda_stream)
+    _call("sgn_check_fp64_solve", _dev(H6, torch.float32, (n, 6)), _dev(g3, torch.float32, (n, 3)), float(lam), n,
+          delta.data_ptr(), pd.data_ptr(), s.cuda_stream)
     s.synchronize()
-    return r
+    return delta, pd != 0
 
 
 # ------------------------------------------------------------------------------- helpers

@@ -270,6 +270,30 @@ sgn_status require_ready(const sgn_plan* p) {
     return SGN_OK;
 }
 
+// The square tile mapping of plain launches covers every tile exactly once (checked at compile
+// time on ragged tile grids for every block shape).
+constexpr bool square_mapping_is_bijective(int TX, int TY, int groups) {
+    int seen[13 * 11] = {};
+    const int blocks = sgn::square_blocks(TX, TY, groups);
+    for (int b = 0; b < blocks; ++b)
+        for (int g = 0; g < groups; ++g) {
+            const int s = sgn::square_surfel(TX, TY, groups, b, g);
+            if (s >= TX * TY) return false;
+            if (s >= 0) ++seen[s];
+        }
+    for (int s = 0; s < TX * TY; ++s)
+        if (seen[s] != 1) return false;
+    return true;
+}
+constexpr bool square_mapping_checks() {
+    for (int groups = 2; groups <= 32; groups *= 2)
+        for (int TX = 1; TX <= 13; TX += 3)
+            for (int TY = 1; TY <= 11; TY += 2)
+                if (!square_mapping_is_bijective(TX, TY, groups)) return false;
+    return true;
+}
+static_assert(square_mapping_checks(), "square tile mapping");
+
 cudaMemcpyKind kind_to_device(sgn_mem m) { return m == SGN_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
 cudaMemcpyKind kind_from_device(sgn_mem m) { return m == SGN_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
 

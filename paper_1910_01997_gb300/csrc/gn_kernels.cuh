@@ -2,6 +2,7 @@
 // texel dtype by gn_f32.cu / gn_f16.cu / gn_bf16.cu.
 #pragma once
 
+#include <algorithm>
 #include <cstring>
 
 #include "gn_impl.cuh"
@@ -25,15 +26,20 @@ constexpr int gn_min_blocks(int P, int G) { return P * P / G <= 2 ? 3 : (P * P /
 // 16-byte aligned), then, when staging, each group's texel boxes (128-byte aligned).
 __host__ __device__ constexpr int scratch_bytes(int groups, int F) { return groups * group_scratch_words(F) * 4; }
 
+// This thread's surfel in a plain launch (the block's square of tiles); S when its group has none.
+__device__ __forceinline__ int block_surfel(const PlanParams& pp, int G) {
+    const int s = square_surfel(pp.TX, pp.TY, blockDim.x / G, blockIdx.x, threadIdx.x / G);
+    return s < 0 ? pp.S : s;
+}
+
 template <int P, int G, int DT, bool LMA = false>
 __global__ void __launch_bounds__(256, gn_min_blocks(P, G)) k_gn(const __grid_constant__ PlanParams pp, int iters, int mode) {
     __shared__ PlanParams spp;
     extern __shared__ float4 sdyn[];
     load_plan(&spp, &pp);
     __syncthreads();
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     float* scratch = reinterpret_cast<float*>(sdyn) + (threadIdx.x / G) * group_scratch_words(pp.F);
-    gn_surfel<P, G, DT, false, 8, 0, LMA>(&spp, gtid / G, threadIdx.x % G, iters, mode, scratch);
+    gn_surfel<P, G, DT, false, 8, 0, LMA>(&spp, block_surfel(pp, G), threadIdx.x % G, iters, mode, scratch);
 }
 
 // Staged variant: every group of G lanes also owns kStageSlots texel boxes (box_stride(P, DT) bytes
@@ -60,9 +66,8 @@ __global__ void __launch_bounds__(256, gn_min_blocks(P, G))
     st.slots_ptr = dyn + (st.slots - smem_addr(dyn));
     st.issued = st.consumed = 0;
     st.broken = false;
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     float* scratch = reinterpret_cast<float*>(sdyn) + grp * group_scratch_words(pp.F);
-    gn_surfel<P, G, DT, true>(&spp, gtid / G, lg, iters, mode, scratch, &st);
+    gn_surfel<P, G, DT, true>(&spp, block_surfel(pp, G), lg, iters, mode, scratch, &st);
 }
 
 // Circular surfels: one warp per surfel, DPPL disc pixels per lane in passes of four.
@@ -72,9 +77,8 @@ __global__ void __launch_bounds__(256, 2) k_gn_disc(const __grid_constant__ Plan
     extern __shared__ float4 sdyn[];
     load_plan(&spp, &pp);
     __syncthreads();
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     float* scratch = reinterpret_cast<float*>(sdyn) + (threadIdx.x / 32) * group_scratch_words(pp.F);
-    gn_surfel<P, 32, DT, false, 4, DPPL>(&spp, gtid / 32, threadIdx.x % 32, iters, mode, scratch);
+    gn_surfel<P, 32, DT, false, 4, DPPL>(&spp, block_surfel(pp, 32), threadIdx.x % 32, iters, mode, scratch);
 }
 
 template <int P, int DT, int DPPL>
@@ -86,6 +90,9 @@ int launch_disc(const PlanParams& pp, int iters, int mode, int grid, int block, 
         if (e != cudaSuccess) return int(e);
         attr_set = true;
     }
+    static int carveout = -1;
+    const cudaError_t e = prefer_l1(k_gn_disc<P, DT, DPPL>, scratch_bytes(block / 32, pp.F), 2 * 256 / block, carveout);
+    if (e != cudaSuccess) return int(e);
     k_gn_disc<P, DT, DPPL><<<grid, block, scratch_bytes(block / 32, pp.F), st>>>(pp, iters, mode);
     return int(cudaGetLastError());
 }
@@ -99,6 +106,30 @@ int launch_disc_ppl(const PlanParams& pp, int iters, int mode, int grid, int blo
     return int(cudaErrorInvalidConfiguration);
 }
 
+// Ask for the smallest shared-memory carveout that keeps `blocks` blocks of a launch resident
+// (dynamic + static shared memory + the driver's reservation per block), so that the rest of the
+// SM's unified L1/shared storage caches texels: the warped footprints of the resident surfels'
+// frames then stay in L1 from one iteration to the next.  `last` remembers the value set.
+template <typename Kernel>
+inline cudaError_t prefer_l1(Kernel kernel, int dyn_bytes, int blocks, int& last) {
+    static int smem_per_sm = 0;
+    if (smem_per_sm == 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess || smem_per_sm <= 0) return e == cudaSuccess ? cudaErrorInvalidValue : e;
+    }
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const long long need = (long long)blocks * (dyn_bytes + (long long)fa.sharedSizeBytes + 1024);
+    const int pct = int(std::min<long long>(100, (need * 100 + smem_per_sm - 1) / smem_per_sm));
+    if (pct == last) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    if (e == cudaSuccess) last = pct;
+    return e;
+}
+
 template <int P, int G, int DT>
 int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st, const void* tmap) {
     const int scratch = scratch_bytes(block / G, pp.F);
@@ -110,6 +141,9 @@ int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, c
             if (e != cudaSuccess) return int(e);
             attr_set = true;
         }
+        static int carveout = -1;
+        const cudaError_t e = prefer_l1(k_gn<P, G, DT, true>, scratch, gn_min_blocks(P, G) * 256 / block, carveout);
+        if (e != cudaSuccess) return int(e);
         k_gn<P, G, DT, true><<<grid, block, scratch, st>>>(pp, iters, mode);
         return int(cudaGetLastError());
     }
@@ -121,6 +155,9 @@ int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, c
             if (e != cudaSuccess) return int(e);
             attr_set = true;
         }
+        static int carveout = -1;
+        const cudaError_t e = prefer_l1(k_gn<P, G, DT>, scratch, gn_min_blocks(P, G) * 256 / block, carveout);
+        if (e != cudaSuccess) return int(e);
         k_gn<P, G, DT><<<grid, block, scratch, st>>>(pp, iters, mode);
         return int(cudaGetLastError());
     }
@@ -142,10 +179,9 @@ int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, c
 template <int DT>
 int launch_gn_dtype(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap) {
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const long long threads = (long long)pp.S * G;
-    const int grid = int((threads + block - 1) / block);
-    if (grid == 0) return cudaSuccess;
     if (block > 256 || block % G) return int(cudaErrorInvalidConfiguration);
+    const int grid = pp.S > 0 ? square_blocks(pp.TX, pp.TY, block / G) : 0;
+    if (grid == 0) return cudaSuccess;
     if (pp.disc_n > 0) {  // circular surfels: 32 lanes per surfel, no staging
         if (G != 32) return int(cudaErrorInvalidConfiguration);
         switch (pp.P) {

@@ -40,6 +40,23 @@ constexpr int kMapWords = 24;
 constexpr int kFrameWords = kMapOffset + kMapWords;
 SGN_HD constexpr int group_scratch_words(int F) { return F * kFrameWords + 4; }
 
+// Surfels of a plain launch by block: a block's `groups` surfels are an sqx x sqy square of
+// neighbouring tiles (sqx = 2, 2, 4, 4, 8 for 2, 4, 8, 16, 32 groups), so that the warped footprints
+// that the SM's resident blocks gather overlap and stay in its L1 cache across iterations (a row
+// strip of the same tiles covers more texels).  Squares past the right or bottom tile edge have
+// groups without a tile (-1).
+SGN_HD constexpr int square_w(int groups) { return groups >= 32 ? 8 : groups >= 8 ? 4 : groups >= 2 ? 2 : 1; }
+SGN_HD constexpr int square_blocks(int TX, int TY, int groups) {
+    const int sqx = square_w(groups), sqy = groups / sqx;
+    return ((TX + sqx - 1) / sqx) * ((TY + sqy - 1) / sqy);
+}
+SGN_HD constexpr int square_surfel(int TX, int TY, int groups, int block, int group) {
+    const int sqx = square_w(groups), sqy = groups / sqx;
+    const int nsx = (TX + sqx - 1) / sqx;
+    const int x = (block % nsx) * sqx + group % sqx, y = (block / nsx) * sqy + group / sqx;
+    return x < TX && y < TY ? y * TX + x : -1;
+}
+
 // Everything a kernel needs to solve the surfels of one keyframe problem.
 // Lives in kernel parameters (plain launch) or in a device table (batched launch); kernels
 // copy it to shared memory before use.
