@@ -639,7 +639,8 @@ def run_ours(args):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded box-room renders, sigma 0.01 noise)",
         "config": {**WORKLOAD, "l2": (f"inputs larger than L2: steps rotate over {R} keyframe instances "
-                                      f"(~35 MB of traffic each, {R} x 35 MB vs 126 MB L2); no flush"),
+                                      f"(~35 MB of traffic each, {R} x 35 MB vs 126 MB L2); no flush" if R * 35 > 2 * 126
+                                      else f"NOT evicted from L2 ({R} instances of ~35 MB): profiling run only"),
                    "instances": R, "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": profiled_traffic(), "kernel": "k_gn<8,16,f32>",
