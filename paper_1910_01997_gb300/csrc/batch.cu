@@ -110,6 +110,9 @@ int launch_gn_batch(const PlanParams* d_plans, const WorkItem* d_items, int n_it
     e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return int(e);
     const size_t smem = batch_scratch_bytes(max_frames);
+    static int carveout[2] = {-1, -1};
+    e = variant == 0 ? prefer_l1(k_gn_batch<0>, int(smem), 2, carveout[0]) : prefer_l1(k_gn_batch<1>, int(smem), 2, carveout[1]);
+    if (e != cudaSuccess) return int(e);
     if (variant == 0)
         k_gn_batch<0><<<grid, block_threads, smem, st>>>(d_plans, d_items, n_items, d_counter, iters, max_frames);
     else

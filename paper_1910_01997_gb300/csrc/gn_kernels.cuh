@@ -106,30 +106,6 @@ int launch_disc_ppl(const PlanParams& pp, int iters, int mode, int grid, int blo
     return int(cudaErrorInvalidConfiguration);
 }
 
-// Ask for the smallest shared-memory carveout that keeps `blocks` blocks of a launch resident
-// (dynamic + static shared memory + the driver's reservation per block), so that the rest of the
-// SM's unified L1/shared storage caches texels: the warped footprints of the resident surfels'
-// frames then stay in L1 from one iteration to the next.  `last` remembers the value set.
-template <typename Kernel>
-inline cudaError_t prefer_l1(Kernel kernel, int dyn_bytes, int blocks, int& last) {
-    static int smem_per_sm = 0;
-    if (smem_per_sm == 0) {
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        if (e != cudaSuccess || smem_per_sm <= 0) return e == cudaSuccess ? cudaErrorInvalidValue : e;
-    }
-    cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
-    if (e != cudaSuccess) return e;
-    const long long need = (long long)blocks * (dyn_bytes + (long long)fa.sharedSizeBytes + 1024);
-    const int pct = int(std::min<long long>(100, (need * 100 + smem_per_sm - 1) / smem_per_sm));
-    if (pct == last) return cudaSuccess;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    if (e == cudaSuccess) last = pct;
-    return e;
-}
-
 template <int P, int G, int DT>
 int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st, const void* tmap) {
     const int scratch = scratch_bytes(block / G, pp.F);
