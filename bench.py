@@ -358,6 +358,55 @@ def frame_change_leg(prob, stream, reps: int = 50):
             "surfels_per_s": len(s) / (ms * 1e-3), "note": "transfer (Eq. 10) + depth-buffered disc render, 4 launches"}
 
 
+def precision_leg(stream, dev, reps: int = 50):
+    """Config-3 leg: one 1280x720 keyframe, 8 observing frames, 8x8 surfels (14400), texels in
+    FP32, FP16 and BF16 (FP32 arithmetic and accumulation, FP64 solves above the condition-number
+    threshold); CUDA-event time of the solve (seeding, 10 iterations, final cost, depth map) as a
+    graph, and the share of surfels whose solves took the FP64 route."""
+    import numpy as np
+    import torch
+
+    import paper_1910_01997_gb300 as sgn
+    import synth
+
+    prob = synth.room_problem(1, W=1280, H=720, F=8)
+    iters = WORKLOAD["iterations"]
+    res = prob.S * prob.P * prob.P * prob.F * iters
+    out = {"workload": "room1280x720_f8_p8_seed20_it10", "surfels": int(prob.S)}
+    with torch.cuda.stream(stream):
+        kf = torch.from_numpy(prob.keyframe).to(dev)
+        fr = torch.from_numpy(prob.frames).to(dev)
+        id0 = torch.from_numpy(prob.id0.astype(np.float32)).to(dev)
+        n0 = torch.from_numpy(prob.n0.astype(np.float32)).to(dev)
+        st0 = torch.from_numpy(prob.state).to(dev)
+        for dt in ("f32", "f16", "bf16"):
+            plan = sgn.Plan(prob.W, prob.H, prob.P, prob.F, dt, stream=stream)
+            plan.set_intrinsics(*prob.cam)
+            plan.set_keyframe(kf)
+            plan.set_frames([fr[i] for i in range(prob.F)], prob.poses)
+            plan.init_surfels(id0, n0, st0)
+            plan.solve(iters)
+            stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                plan.solve(iters)
+            for _ in range(5):
+                g.replay()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                g.replay()
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b) / reps
+            status = plan.read_surfels()["status"]
+            out[dt] = {"solve_ms": ms, "residuals_per_s": res / (ms * 1e-3),
+                       "fp64_routed_surfels": int(((status & 0x80) != 0).sum())}
+            plan._keep.clear()
+            plan.close()
+    return out
+
+
 def serving_leg(duration_s: float, dev, streams: int = 16, rate_hz: float = 5.0, burst: int = 96):
     """Config-5 leg: 16 simulated camera streams submit keyframe solves (Poisson arrivals, 5/s per
     stream; half 640x480, half 1280x720; 8x8 surfels, 4 frames, FP16 texels, 10 iterations) to the
@@ -684,6 +733,7 @@ def run_ours(args):
         line["batch"] = [batch_leg(dt, stream, dev) for dt in ("f32", "f16")]
         line["ablation"] = ablation_leg(prob, stream)
         line["frame_change"] = frame_change_leg(prob, stream)
+        line["precision"] = precision_leg(stream, dev)
     if rank == 0 and args.serve_seconds > 0:
         line["serving"] = serving_leg(args.serve_seconds, dev)
     if rank == 0 and not args.no_cpu_baseline:
