@@ -39,10 +39,17 @@ KERNEL_SOURCES = ["paper_1910_01997_gb300/csrc/gn_impl.cuh", "paper_1910_01997_g
                   "paper_1910_01997_gb300/csrc/gn_f32.cu"]
 
 
-def kernel_sha() -> str:
+def kernel_sha(root: str = ROOT) -> str:
+    """Hash of the Gauss-Newton kernel's sources with comments and blank lines removed (a comment
+    edit does not invalidate the committed DRAM counters; any code change does)."""
+    import re
+
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, rel), "rb").read())
+        text = open(os.path.join(root, rel)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 
