@@ -586,9 +586,8 @@ class StepInstance:
     def post(self, host=False):
         sgn, o = self.sgn, (self.host_out if host else self.out)
         mem = sgn.SGN_HOST if host else sgn.SGN_DEVICE
-        sgn.sgn_read_surfels(self.plan.handle, o["id"].data_ptr(), o["n"].data_ptr(), o["cost"].data_ptr(),
-                             o["nres"].data_ptr(), o["status"].data_ptr(), mem)
-        sgn.sgn_read_depth_map(self.plan.handle, o["depth"].data_ptr(), o["sidx"].data_ptr(), mem)
+        sgn.sgn_read_results(self.plan.handle, *[o[k].data_ptr() for k in ("id", "n", "cost", "nres", "status", "depth", "sidx")],
+                             mem)
 
     def step(self):
         self.pre()

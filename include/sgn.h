@@ -174,6 +174,14 @@ sgn_status sgn_read_surfels(sgn_plan* plan, float* inv_depth, float* normal, flo
  * generating surfel index (W x H int32, -1 where none), tightly packed rows (Sec. 2.2). */
 sgn_status sgn_read_depth_map(sgn_plan* plan, float* inv_depth, int32_t* surfel_index, sgn_mem mem);
 
+/* sgn_read_surfels and sgn_read_depth_map in one call: the surfels (Sec. 2.1: inverse depth,
+ * normal, last cost, valid samples, status) and the per-pixel inverse depth and surfel index
+ * (Sec. 2.2), layouts as there.  Any pointer may be NULL.  With SGN_DEVICE memory every transfer
+ * of the call is one copy kernel; with SGN_HOST one cudaMemcpyAsync per array.  Valid after
+ * sgn_sync. */
+sgn_status sgn_read_results(sgn_plan* plan, float* inv_depth, float* normal, float* cost, int32_t* nres,
+                            uint8_t* status, float* depth_map, int32_t* surfel_index, sgn_mem mem);
+
 /* Wait for the plan's stream; timeout_ns = 0 waits forever.  SGN_ERR_TIMEOUT if the
  * deadline passes (the work keeps running), SGN_ERR_CUDA on an asynchronous error. */
 sgn_status sgn_sync(sgn_plan* plan, uint64_t timeout_ns);

@@ -93,6 +93,7 @@ _SIGS = {
     "sgn_solve": [_P, _I],
     "sgn_read_surfels": [_P, _P, _P, _P, _P, _P, _I],
     "sgn_read_depth_map": [_P, _P, _P, _I],
+    "sgn_read_results": [_P, _P, _P, _P, _P, _P, _P, _P, _I],
     "sgn_sync": [_P, ctypes.c_uint64],
     "sgn_state_bytes": [_P, ctypes.POINTER(_SZ)],
     "sgn_export_state": [_P, _P, _SZ],
@@ -232,6 +233,10 @@ def sgn_read_surfels(plan, id_ptr, n_ptr, cost_ptr, nres_ptr, status_ptr, mem):
 
 def sgn_read_depth_map(plan, depth_ptr, sidx_ptr, mem):
     _call("sgn_read_depth_map", plan, depth_ptr, sidx_ptr, mem)
+
+
+def sgn_read_results(plan, id_ptr, n_ptr, cost_ptr, nres_ptr, status_ptr, depth_ptr, sidx_ptr, mem):
+    _call("sgn_read_results", plan, id_ptr, n_ptr, cost_ptr, nres_ptr, status_ptr, depth_ptr, sidx_ptr, mem)
 
 
 def sgn_sync(plan, timeout_ns=0):

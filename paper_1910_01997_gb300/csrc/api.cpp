@@ -705,23 +705,40 @@ static sgn_status run_mode(sgn_plan* p, int iters, int mode) {
 sgn_status sgn_run(sgn_plan* p, int iters) { return run_mode(p, iters, sgn::kModeRun); }
 sgn_status sgn_solve(sgn_plan* p, int iters) { return run_mode(p, iters, sgn::kModeSolve); }
 
-sgn_status sgn_read_surfels(sgn_plan* p, float* id, float* n, float* cost, int32_t* nres, uint8_t* status, sgn_mem mem) {
-    sgn_status st = require_bound(p);
-    if (st != SGN_OK) return st;
-    if (!p->surfels_set) return fail(SGN_ERR_STATE, "surfels not initialised");
-    if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
-    DeviceGuard g(p->device);
-    if ((st = ensure_state(p)) != SGN_OK) return st;
-    const size_t S = size_t(p->S);
-    Transfers t;
-    if (id) t.add(id, p->ws + p->L.id, S * sizeof(float));
-    if (n) t.add(n, p->ws + p->L.n, 3 * S * sizeof(float));
-    if (cost) t.add(cost, p->ws + p->L.cost, S * sizeof(float));
-    if (nres) t.add(nres, p->ws + p->L.nres, S * sizeof(int32_t));
-    if (status) t.add(status, p->ws + p->L.status, S);
-    const cudaError_t e = t.issue(mem, kind_from_device(mem), p->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "surfel readback");
+// Transfers of the surfel arrays and of the depth map into t (the map is rendered first when it is
+// stale).  Either group may be absent (all its pointers NULL).
+static sgn_status queue_results(sgn_plan* p, float* id, float* n, float* cost, int32_t* nres, uint8_t* status,
+                                float* inv_depth, int32_t* sidx, bool surfels, bool map, Transfers& t) {
+    sgn_status st;
+    if (surfels) {
+        if (!p->surfels_set) return fail(SGN_ERR_STATE, "surfels not initialised");
+        if ((st = ensure_state(p)) != SGN_OK) return st;
+        const size_t S = size_t(p->S);
+        if (id) t.add(id, p->ws + p->L.id, S * sizeof(float));
+        if (n) t.add(n, p->ws + p->L.n, 3 * S * sizeof(float));
+        if (cost) t.add(cost, p->ws + p->L.cost, S * sizeof(float));
+        if (nres) t.add(nres, p->ws + p->L.nres, S * sizeof(int32_t));
+        if (status) t.add(status, p->ws + p->L.status, S);
+    }
+    if (map) {
+        if (!p->depth_valid) {
+            if (!p->have_K || !p->surfels_set) return fail(SGN_ERR_STATE, "depth map needs intrinsics and surfels");
+            if ((st = ensure_state(p)) != SGN_OK) return st;
+            PlanParams pp = make_params(p);
+            int e = p->disc.empty() ? sgn::launch_render_depth(pp, p->stream) : sgn::launch_render_discs(pp, p->stream);
+            if (e) return cuda_fail(e, "depth render launch");
+            sgn::count_launch(p->disc.empty() ? 1 : 2);
+            p->depth_valid = true;
+        }
+        const size_t npx = size_t(p->desc.width) * p->desc.height;
+        if (inv_depth) t.add(inv_depth, p->ws + p->L.depth, npx * sizeof(float));
+        if (sidx) t.add(sidx, p->ws + p->L.sidx, npx * sizeof(int32_t));
+    }
     return SGN_OK;
+}
+
+sgn_status sgn_read_surfels(sgn_plan* p, float* id, float* n, float* cost, int32_t* nres, uint8_t* status, sgn_mem mem) {
+    return sgn_read_results(p, id, n, cost, nres, status, nullptr, nullptr, mem);
 }
 
 sgn_status sgn_read_depth_map(sgn_plan* p, float* inv_depth, int32_t* sidx, sgn_mem mem) {
@@ -729,21 +746,25 @@ sgn_status sgn_read_depth_map(sgn_plan* p, float* inv_depth, int32_t* sidx, sgn_
     if (st != SGN_OK) return st;
     if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
     DeviceGuard g(p->device);
-    if (!p->depth_valid) {
-        if (!p->have_K || !p->surfels_set) return fail(SGN_ERR_STATE, "depth map needs intrinsics and surfels");
-        if ((st = ensure_state(p)) != SGN_OK) return st;
-        PlanParams pp = make_params(p);
-        int e = p->disc.empty() ? sgn::launch_render_depth(pp, p->stream) : sgn::launch_render_discs(pp, p->stream);
-        if (e) return cuda_fail(e, "depth render launch");
-        sgn::count_launch(p->disc.empty() ? 1 : 2);
-        p->depth_valid = true;
-    }
-    const size_t npx = size_t(p->desc.width) * p->desc.height;
     Transfers t;
-    if (inv_depth) t.add(inv_depth, p->ws + p->L.depth, npx * sizeof(float));
-    if (sidx) t.add(sidx, p->ws + p->L.sidx, npx * sizeof(int32_t));
+    if ((st = queue_results(p, nullptr, nullptr, nullptr, nullptr, nullptr, inv_depth, sidx, false, true, t)) != SGN_OK)
+        return st;
     const cudaError_t e = t.issue(mem, kind_from_device(mem), p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "depth map readback");
+    return SGN_OK;
+}
+
+sgn_status sgn_read_results(sgn_plan* p, float* id, float* n, float* cost, int32_t* nres, uint8_t* status,
+                            float* inv_depth, int32_t* sidx, sgn_mem mem) {
+    sgn_status st = require_bound(p);
+    if (st != SGN_OK) return st;
+    if (mem != SGN_HOST && mem != SGN_DEVICE) return fail(SGN_ERR_INVALID_ARGUMENT, "bad memory kind");
+    DeviceGuard g(p->device);
+    Transfers t;
+    const bool map = inv_depth || sidx;
+    if ((st = queue_results(p, id, n, cost, nres, status, inv_depth, sidx, true, map, t)) != SGN_OK) return st;
+    const cudaError_t e = t.issue(mem, kind_from_device(mem), p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "result readback");
     return SGN_OK;
 }
 

@@ -197,6 +197,45 @@ def test_device_inputs_equal_host_inputs():
         assert np.array_equal(dev[k].cpu().numpy(), host[k]), k
 
 
+def test_read_results_equals_separate_readbacks():
+    """sgn_read_results (one call; one copy kernel for device memory) returns what sgn_read_surfels
+    and sgn_read_depth_map return, into device and into host memory, with any pointer left NULL."""
+    import torch
+
+    import paper_1910_01997_gb300 as sgn
+
+    prob = synth.room_problem(3)
+    plan = sgn.Plan(prob.W, prob.H, prob.P, prob.F)
+    plan.set_intrinsics(*prob.cam)
+    plan.set_keyframe(prob.keyframe)
+    plan.set_frames(prob.frames, prob.poses)
+    plan.init_surfels(prob.id0.astype(np.float32), prob.n0.astype(np.float32), prob.state)
+    plan.solve(4)
+    ref = plan.read_surfels()
+    ref_depth, ref_sidx = plan.read_depth_map()
+    S, H, W = prob.S, prob.H, prob.W
+    shapes = dict(id=((S,), torch.float32), n=((S, 3), torch.float32), cost=((S,), torch.float32),
+                  nres=((S,), torch.int32), status=((S,), torch.uint8), depth=((H, W), torch.float32),
+                  sidx=((H, W), torch.int32))
+    for device in (True, False):
+        out = {k: (torch.empty(*sh, dtype=dt, device="cuda") if device else torch.empty(*sh, dtype=dt).pin_memory())
+               for k, (sh, dt) in shapes.items()}
+        sgn.sgn_read_results(plan.handle, *[out[k].data_ptr() for k in shapes], sgn.SGN_DEVICE if device else sgn.SGN_HOST)
+        plan.sync()
+        for k in ("id", "n", "cost", "nres", "status"):
+            assert np.array_equal(out[k].cpu().numpy(), ref[k]), (device, k)
+        assert np.array_equal(out["depth"].cpu().numpy(), ref_depth) and np.array_equal(out["sidx"].cpu().numpy(), ref_sidx)
+    # NULL pointers: only the depth map, then only the costs
+    d = torch.zeros(H, W, device="cuda")
+    sgn.sgn_read_results(plan.handle, 0, 0, 0, 0, 0, d.data_ptr(), 0, sgn.SGN_DEVICE)
+    c = torch.zeros(S, device="cuda")
+    sgn.sgn_read_results(plan.handle, 0, 0, c.data_ptr(), 0, 0, 0, 0, sgn.SGN_DEVICE)
+    plan.sync()
+    assert np.array_equal(d.cpu().numpy(), ref_depth) and np.array_equal(c.cpu().numpy(), ref["cost"])
+    with pytest.raises(sgn.SgnError):
+        sgn.sgn_read_results(plan.handle, 0, 0, 0, 0, 0, 0, 0, 7)
+
+
 def test_edge_cases():
     prob = synth.tiny_problem(1)
     # all empty
