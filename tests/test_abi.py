@@ -89,6 +89,12 @@ def test_calls_on_an_unbound_plan_fail_cleanly(sgn):
     with pytest.raises(sgn.SgnError):
         sgn.sgn_set_intrinsics(h, -1.0, 1.0, 0.0, 0.0)
     sgn.sgn_set_intrinsics(h, 56.0, 56.0, 31.5, 31.5)
+    for call in (lambda: sgn.sgn_read_results(h, 0, 0, 0, 0, 0, 0, 0, sgn.SGN_DEVICE),
+                 lambda: sgn.sgn_read_surfels(h, 0, 0, 0, 0, 0, sgn.SGN_HOST),
+                 lambda: sgn.sgn_read_depth_map(h, 0, 0, sgn.SGN_HOST)):
+        with pytest.raises(sgn.SgnError) as e:
+            call()
+        assert e.value.status == sgn.SGN_ERR_NOT_BOUND
     sgn.sgn_plan_destroy(h)
 
 
