@@ -169,14 +169,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def profiled_counters():
+    """ncu counters of one Gauss-Newton launch from the committed summary (DRAM bytes, warp
+    instructions), when they were taken on the current kernel source; else an empty dict."""
+    path = os.path.join(ROOT, "profiles", "gn_room640_traffic.json")
+    if not os.path.exists(path):
+        return {}
+    d = json.load(open(path))
+    return d if d.get("kernel_sha") == kernel_sha() else {}
+
+
 def profiled_traffic():
     """DRAM bytes per launch of the Gauss-Newton kernel from the committed ncu summary, when it
     was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "gn_room640_traffic.json")
-    if not os.path.exists(path):
-        return None
-    d = json.load(open(path))
-    return d.get("dram_bytes_per_launch") if d.get("kernel_sha") == kernel_sha() else None
+    return profiled_counters().get("dram_bytes_per_launch")
 
 
 def cpu_baseline(prob, budget_s: float = 10.0):
@@ -624,6 +630,25 @@ class StepInstance:
         return launches
 
 
+def issue_roofline(kernel_s: float, clocks: dict, dev):
+    """What bounds the Gauss-Newton kernel: its warp-instruction issue rate (ncu instruction count
+    of one launch on the current source / the live kernel time) against one instruction per cycle
+    on every SM sub-partition (4 per SM) at the SM clock sampled during the timed region."""
+    import torch
+
+    inst = profiled_counters().get("warp_instructions_per_launch")
+    if inst is None:
+        return None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz")
+    if not mhz:
+        return None
+    achieved = inst / kernel_s / 1e9
+    peak = sms * 4 * mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G warp instructions/s", "frac": achieved / peak,
+            "instructions_per_launch": inst, "note": "1 warp instruction per cycle per SM sub-partition at the sampled SM clock"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -730,6 +755,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "public API calls per step from page-locked host buffers, steps enqueued back to back on two "
                         "streams (alternate plans), one synchronisation when the last step's results are on the host"},
+        "issue": issue_roofline(kern_avg_s, clk, dev),
         "gpu_launches": int(launches),
         "step_graphs": "one CUDA graph replay per step (uploads + frame prep, solve, readback)",
         "kernel_ms_per_step": statistics.mean(kern_ms),
