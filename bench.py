@@ -5,9 +5,10 @@ keyframe and 5 observing frames, 8x8 surfels (4800), 20 % of them seeded from ne
 sigma 0.01, 10 Gauss-Newton iterations.  A step uploads the keyframe and surfels, prepares the
 frames (intensity + gradient texels), seeds, iterates, evaluates the final cost and renders the
 inverse-depth map, then copies the surfels and the map out; it is captured once as one CUDA graph
-and replayed.  Inputs are resident in device memory when the timed region starts; the steps rotate
-over 16 independent keyframe instances (different seeds), so a step's inputs have left the L2 cache
-by the time it runs again, and K steps are timed back to back as one region.  The Gauss-Newton
+and replayed, the plans alternating between two streams.  Inputs are resident in device memory when
+the timed region starts; the steps rotate over 16 independent keyframe instances (different seeds),
+so a step's inputs have left the L2 cache by the time it runs again, and K steps are timed back to
+back as one region (also reported on one stream, `one_stream`).  The Gauss-Newton
 kernel is timed in a second pass of the K steps with the solve as a graph of its own between CUDA
 events.  "e2e" repeats the steps through the C ABI from page-locked host buffers, host<->device
 copies included, enqueued back to back with the plans alternating between two streams (the
@@ -677,21 +678,41 @@ def run_ours(args):
             insts[i % R].graph.replay()
         stream.synchronize()
 
-        # (1) the headline: K whole steps, one CUDA graph each, back to back
-        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # (1) the headline: K whole steps, one CUDA graph each, back to back, each replayed on its
+        # plan's stream (two streams: a step's kernels fill the tail of the previous step's
+        # Gauss-Newton wave); then the same K steps one after another on one stream
+        def timed_steps(two_streams: bool) -> float:
+            start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            if two_streams:
+                streams[1].wait_event(start)
+            for i in range(args.steps):
+                inst = insts[i % R]
+                if two_streams:
+                    with torch.cuda.stream(inst.stream):
+                        inst.graph.replay()
+                else:
+                    inst.graph.replay()
+            if two_streams:
+                joined = torch.cuda.Event()
+                joined.record(streams[1])
+                stream.wait_event(joined)
+            end.record(stream)
+            stream.synchronize()
+            return start.elapsed_time(end)
+
         ranks.barrier()
         torch.cuda.synchronize()
         with ClockSampler(local) as clocks:
             time.sleep(0.3)
-            start.record(stream)
-            for i in range(args.steps):
-                insts[i % R].graph.replay()
-            end.record(stream)
-            stream.synchronize()
+            total_ms = timed_steps(True)
         torch.cuda.synchronize()
         ranks.barrier()
-        total_ms = ranks.max_ms(start.elapsed_time(end))
+        total_ms = ranks.max_ms(total_ms)
         launches = launches_per_step * args.steps
+        ranks.barrier()
+        one_ms = ranks.max_ms(timed_steps(False))
+        ranks.barrier()
 
         # (2) the Gauss-Newton kernel alone: the same K steps with the solve graph bracketed by events
         kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -741,7 +762,9 @@ def run_ours(args):
         "value": value, "unit": "residuals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded box-room renders, sigma 0.01 noise)",
-        "config": {**WORKLOAD, "l2": (f"inputs larger than L2: steps rotate over {R} keyframe instances "
+        "one_stream": {"value": ranks.throughput(res * args.steps, one_ms), "ms_per_step": one_ms / args.steps,
+                       "note": "the same K graph replays one after another on one stream"},
+        "config": {**WORKLOAD, "streams": 2, "l2": (f"inputs larger than L2: steps rotate over {R} keyframe instances "
                                       f"(~35 MB of traffic each, {R} x 35 MB vs 126 MB L2); no flush" if R * 35 > 2 * 126
                                       else f"NOT evicted from L2 ({R} instances of ~35 MB): profiling run only"),
                    "instances": R, "parallelism": f"replicas x{world}"},
@@ -757,7 +780,7 @@ def run_ours(args):
                         "streams (alternate plans), one synchronisation when the last step's results are on the host"},
         "issue": issue_roofline(kern_avg_s, clk, dev),
         "gpu_launches": int(launches),
-        "step_graphs": "one CUDA graph replay per step (uploads + frame prep, solve, readback)",
+        "step_graphs": "one CUDA graph replay per step (uploads + frame prep, solve, readback), alternating between two streams",
         "kernel_ms_per_step": statistics.mean(kern_ms),
         "clocks": clk,
     }
