@@ -5,14 +5,14 @@ keyframe and 5 observing frames, 8x8 surfels (4800), 20 % of them seeded from ne
 sigma 0.01, 10 Gauss-Newton iterations.  A step uploads the keyframe and surfels, prepares the
 frames (intensity + gradient texels), seeds, iterates, evaluates the final cost and renders the
 inverse-depth map, then copies the surfels and the map out; it is captured once as one CUDA graph
-and replayed, the plans alternating between two streams.  Inputs are resident in device memory when
+and replayed, the plans alternating between four streams.  Inputs are resident in device memory when
 the timed region starts; the steps rotate over 16 independent keyframe instances (different seeds),
 so a step's inputs have left the L2 cache by the time it runs again, and K steps are timed back to
 back as one region (also reported on one stream, `one_stream`).  The Gauss-Newton
 kernel is timed in a second pass of the K steps with the solve as a graph of its own between CUDA
 events.  "e2e" repeats the steps through the C ABI from page-locked host buffers, host<->device
-copies included, enqueued back to back with the plans alternating between two streams (the
-host's calls and copies for one step overlap the device's work on the previous one).
+copies included, enqueued back to back on the same streams (the host's calls and copies for one
+step overlap the device's work on the previous ones).
 
 Multi-GPU: keyframes are independent, so N ranks run N independent replicas (weak scaling, no
 collective on the data path); the time is the maximum over ranks.
@@ -666,11 +666,13 @@ def run_ours(args):
     # inputs from L2 before it runs again, so every step starts from HBM without an L2 flush between
     # steps, and the K steps are timed as one region.
     R = args.instances
-    # Plans alternate between two streams: the graph replays of (1) and (2) all run on `stream`, while
-    # the end-to-end leg (3) uses each plan's own stream, so that one step's host<->device copies
-    # overlap the neighbouring step's kernels (as a caller with two streams would run them).
-    streams = [stream, torch.cuda.Stream(device=dev)]
-    insts = [StepInstance(sgn, make_problem(rank * R + i), streams[i % 2], dev) for i in range(R)]
+    # Plans alternate between --streams streams (4): the headline replays each step's graph on its
+    # plan's stream and the end-to-end leg calls the API on it, so that consecutive keyframes overlap
+    # (one step's copies and short kernels and the start of its Gauss-Newton wave fill the previous
+    # steps' tails, as a caller with several streams would run them); the kernel timing pass (2)
+    # and the one-stream figure replay everything on `stream`.
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(max(1, args.streams) - 1)]
+    insts = [StepInstance(sgn, make_problem(rank * R + i), streams[i % len(streams)], dev) for i in range(R)]
     prob = insts[0].prob
     with torch.cuda.stream(stream):
         launches_per_step = [inst.capture() for inst in insts][0]
@@ -679,24 +681,25 @@ def run_ours(args):
         stream.synchronize()
 
         # (1) the headline: K whole steps, one CUDA graph each, back to back, each replayed on its
-        # plan's stream (two streams: a step's kernels fill the tail of the previous step's
-        # Gauss-Newton wave); then the same K steps one after another on one stream
-        def timed_steps(two_streams: bool) -> float:
+        # plan's stream; then the same K steps one after another on one stream
+        def timed_steps(own_streams: bool) -> float:
             start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             start.record(stream)
-            if two_streams:
-                streams[1].wait_event(start)
+            if own_streams:
+                for st in streams[1:]:
+                    st.wait_event(start)
             for i in range(args.steps):
                 inst = insts[i % R]
-                if two_streams:
+                if own_streams:
                     with torch.cuda.stream(inst.stream):
                         inst.graph.replay()
                 else:
                     inst.graph.replay()
-            if two_streams:
-                joined = torch.cuda.Event()
-                joined.record(streams[1])
-                stream.wait_event(joined)
+            if own_streams:
+                for st in streams[1:]:
+                    joined = torch.cuda.Event()
+                    joined.record(st)
+                    stream.wait_event(joined)
             end.record(stream)
             stream.synchronize()
             return start.elapsed_time(end)
@@ -737,12 +740,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         ranks.barrier()
         e0.record(stream)
-        streams[1].wait_event(e0)
+        for st in streams[1:]:
+            st.wait_event(e0)
         for i in range(args.steps):
             insts[i % R].e2e_step(sync=False)
-        joined = torch.cuda.Event()
-        joined.record(streams[1])
-        stream.wait_event(joined)
+        for st in streams[1:]:
+            joined = torch.cuda.Event()
+            joined.record(st)
+            stream.wait_event(joined)
         e1.record(stream)
         torch.cuda.synchronize()
         ranks.barrier()
@@ -764,7 +769,7 @@ def run_ours(args):
         "dtype": "f32", "data": "synthetic (seeded box-room renders, sigma 0.01 noise)",
         "one_stream": {"value": ranks.throughput(res * args.steps, one_ms), "ms_per_step": one_ms / args.steps,
                        "note": "the same K graph replays one after another on one stream"},
-        "config": {**WORKLOAD, "streams": 2, "l2": (f"inputs larger than L2: steps rotate over {R} keyframe instances "
+        "config": {**WORKLOAD, "streams": len(streams), "l2": (f"inputs larger than L2: steps rotate over {R} keyframe instances "
                                       f"(~35 MB of traffic each, {R} x 35 MB vs 126 MB L2); no flush" if R * 35 > 2 * 126
                                       else f"NOT evicted from L2 ({R} instances of ~35 MB): profiling run only"),
                    "instances": R, "parallelism": f"replicas x{world}"},
@@ -776,11 +781,11 @@ def run_ours(args):
                               "with the step split into three graphs")},
         "e2e": {"value": ranks.throughput(res * args.steps, e2e_ms), "unit": "residuals/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "note": "public API calls per step from page-locked host buffers, steps enqueued back to back on two "
-                        "streams (alternate plans), one synchronisation when the last step's results are on the host"},
+                "note": f"public API calls per step from page-locked host buffers, steps enqueued back to back on "
+                        f"{len(streams)} streams (plans alternate), one synchronisation when the last step's results are on the host"},
         "issue": issue_roofline(kern_avg_s, clk, dev),
         "gpu_launches": int(launches),
-        "step_graphs": "one CUDA graph replay per step (uploads + frame prep, solve, readback), alternating between two streams",
+        "step_graphs": f"one CUDA graph replay per step (uploads + frame prep, solve, readback), plans alternating between {len(streams)} streams",
         "kernel_ms_per_step": statistics.mean(kern_ms),
         "clocks": clk,
     }
@@ -838,6 +843,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-keyframe batched leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="duration of the serving leg (0 skips it)")
     ap.add_argument("--instances", type=int, default=16, help="keyframe instances the steps rotate over (L2 eviction)")
+    ap.add_argument("--streams", type=int, default=4, help="streams the keyframe instances alternate between")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
