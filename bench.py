@@ -207,7 +207,8 @@ def cpu_baseline(prob, budget_s: float = 10.0):
 def batch_leg(dtype: str, stream, dev, reps: int = 5):
     """Config-4 leg: 64 keyframes of uneven size (320x240 .. 1920x1080, 4/8/16 px surfels, 2-8
     frames), solved (a) one launch per keyframe, eager; (b) the same launches captured in one CUDA
-    graph; (c) one persistent batch launch with the autotuned schedule.  Returns residuals/s of each
+    graph; (c) one persistent batch launch with the autotuned schedule; (d) as (b) with the plans
+    alternating between four streams.  Returns residuals/s of each
     and the distribution of inverse-depth differences between (c) and (a) (the two are compiled
     separately, so chaotic surfels may round apart; parity is tested against the oracle)."""
     import numpy as np
@@ -268,11 +269,48 @@ def batch_leg(dtype: str, stream, dev, reps: int = 5):
             diffs.append(np.abs(got["id"][m] / ref["id"][m] - 1))
         diffs = np.concatenate(diffs)
         batch.close()
+
+        # (d) the plain launches with the keyframes' plans alternating between four streams (one
+        # graph, forked and joined across the streams)
+        sts = [stream] + [torch.cuda.Stream(device=dev) for _ in range(3)]
+        plans4 = []
+        for i, pr in enumerate(probs):
+            pl = sgn.Plan(pr.W, pr.H, pr.P, pr.F, dtype, stream=sts[i % 4])
+            pl.set_intrinsics(*pr.cam)
+            pl.set_keyframe(keep[2 * i])
+            fr = keep[2 * i + 1]
+            pl.set_frames([fr[k] for k in range(pr.F)], pr.poses)
+            pl.init_surfels(pr.id0, pr.n0, pr.state)
+            plans4.append(pl)
+        torch.cuda.synchronize()
+
+        def plain4():
+            fork = torch.cuda.Event()
+            fork.record(stream)
+            for st in sts[1:]:
+                st.wait_event(fork)
+            for pl in plans4:
+                pl.solve(iters)
+            for st in sts[1:]:
+                join = torch.cuda.Event()
+                join.record(st)
+                stream.wait_event(join)
+
+        plain4()
+        torch.cuda.synchronize()
+        g4 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g4, stream=stream):
+            plain4()
+        ms_graph4 = timed(g4.replay)
+        for pl in plans4:
+            pl._keep.clear()
+            pl.close()
     S = [pr.S for pr in probs]
     return {"texels": dtype, "keyframes": len(probs), "surfels_total": int(sum(S)), "surfels_min": int(min(S)),
             "surfels_max": int(max(S)), "residuals_per_run": int(res),
             "plain_eager": res / (ms_plain / 1e3), "plain_graph": res / (ms_graph / 1e3),
             "batched": res / (ms_batch / 1e3), "speedup_vs_plain_graph": ms_graph / ms_batch,
+            "plain_graph_4_streams": res / (ms_graph4 / 1e3), "speedup_vs_plain_graph_4_streams": ms_graph4 / ms_batch,
             "schedule": {"variant": variant, "surfels_per_item": chunk},
             "depth_rel_diff_vs_plain": {"median": float(np.median(diffs)), "p99": float(np.percentile(diffs, 99)),
                                         "frac_above_1e-4": float(np.mean(diffs > 1e-4))},
