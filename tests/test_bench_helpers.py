@@ -1,0 +1,44 @@
+"""Host-side helpers of the benchmark (CPU only): the kernel source hash that keys the committed
+ncu counters, and the arithmetic of the whole-job figures."""
+import os
+import shutil
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _copy_sources(tmp_path):
+    for rel in bench.KERNEL_SOURCES:
+        dst = tmp_path / rel
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(ROOT, rel), dst)
+    return str(tmp_path)
+
+
+def test_kernel_hash_ignores_comments_but_not_code(tmp_path):
+    root = _copy_sources(tmp_path)
+    h0 = bench.kernel_sha(root)
+    assert h0 == bench.kernel_sha()
+    src = tmp_path / bench.KERNEL_SOURCES[0]
+    text = src.read_text()
+    src.write_text("// a new comment line\n" + text.replace("namespace sgn {", "namespace sgn {  /* inline */", 1) + "\n\n")
+    assert bench.kernel_sha(root) == h0
+    src.write_text(text.replace("SGN_CHUNK 2", "SGN_CHUNK 3", 1))
+    assert bench.kernel_sha(root) != h0
+
+
+def test_committed_counters_match_the_current_kernel():
+    c = bench.profiled_counters()
+    if not c:
+        pytest.skip("the committed ncu counters were taken on other kernel sources (the bench reports them as null)")
+    assert c["dram_bytes_per_launch"] > 0 and c["warp_instructions_per_launch"] > 0
+
+
+def test_single_rank_throughput_and_ms():
+    ranks = bench.Ranks("gloo")
+    assert ranks.throughput(15_360_000 * 1000, 80.0) == pytest.approx(1.92e11)
