@@ -186,22 +186,56 @@ def profiled_traffic():
     return profiled_counters().get("dram_bytes_per_launch")
 
 
-def cpu_baseline(prob, budget_s: float = 10.0):
-    """The FP64 oracle (as it stands) on the host cores: whole keyframe solves for ~budget_s."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo; Arm cores report implementer/part codes)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return name
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model", "CPU part"):
+        for line in info.splitlines():
+            if line.split(":")[0].strip() == key:
+                return f"{key}: {line.split(':', 1)[1].strip()}"
+    return "unknown"
+
+
+def time_oracle(prob, budget_s: float, nthreads: int = 0):
+    """Whole keyframe solves of the FP64 oracle (as it stands) for about budget_s: (residuals/s,
+    solves, seconds, threads used)."""
     import oracle
 
     ob = oracle.Problem.from_synth(prob)
     prm = oracle.params()
     n, t0, threads = 0, time.perf_counter(), 0
     while True:
-        out = ob.solve(prm, WORKLOAD["iterations"], prob.id0, prob.n0, prob.state, depth_map=True)
+        out = ob.solve(prm, WORKLOAD["iterations"], prob.id0, prob.n0, prob.state, nthreads=nthreads, depth_map=True)
         threads = out["threads"]
         n += 1
         dt = time.perf_counter() - t0
         if dt >= budget_s:
             break
-    return {"value": n * residuals_per_step(prob) / dt, "unit": "residuals/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n} whole keyframe solves of the benchmark workload ({dt:.1f} s, FP64 C, OpenMP over surfels)"}
+    return n * residuals_per_step(prob) / dt, n, dt, threads
+
+
+def cpu_baseline(prob, budget_s: float = 10.0):
+    """The FP64 oracle on the host: all cores (OpenMP over surfels) for ~budget_s, then one thread for
+    ~budget_s / 2, with the CPU model."""
+    value, n, dt, threads = time_oracle(prob, budget_s)
+    v1, n1, dt1, _ = time_oracle(prob, budget_s / 2, nthreads=1)
+    return {"value": value, "unit": "residuals/s", "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
+            "single_thread": {"value": v1, "unit": "residuals/s", "cores": 1,
+                              "sample": f"{n1} whole keyframe solves ({dt1:.1f} s, one thread)"},
+            "sample": f"{n} whole keyframe solves of the benchmark workload ({dt:.1f} s, FP64 C, OpenMP over surfels "
+                      f"on {threads} threads)"}
 
 
 def batch_leg(dtype: str, stream, dev, reps: int = 5):
@@ -459,12 +493,15 @@ def precision_leg(stream, dev, reps: int = 50):
     return out
 
 
-def serving_leg(duration_s: float, dev, streams: int = 16, rate_hz: float = 5.0, burst: int = 96):
-    """Config-5 leg: 16 simulated camera streams submit keyframe solves (Poisson arrivals, 5/s per
-    stream; half 640x480, half 1280x720; 8x8 surfels, 4 frames, FP16 texels, 10 iterations) to the
-    serving loop for duration_s seconds (open loop: per-keyframe latency p50/p99/max).  Then a burst
-    of requests measures saturated throughput, against plain per-keyframe upload + solve + readback
-    launches of the same requests on one stream."""
+def serving_leg(duration_s: float, dev, streams: int = 16, rate_hz: float = 5.0, burst: int = 96,
+                loads=(0.5, 0.9)):
+    """Config-5 leg: 16 simulated camera streams submit keyframe solves (Poisson arrivals; half the
+    streams 640x480, half 1280x720; 8x8 surfels, 4 frames, FP16 texels, 10 iterations) to the serving
+    loop.  First three saturated bursts of the request mix measure the served throughput (against
+    plain per-keyframe upload + solve + readback launches of the same requests on one stream); then
+    open-loop runs of duration_s seconds each at the nominal rate (5 keyframes/s per stream) and at
+    the given fractions of the saturated throughput (per-stream Poisson rate scaled) report the
+    per-keyframe latency (submission to results in host memory) p50/p99/max."""
     import numpy as np
     import torch
 
@@ -481,6 +518,7 @@ def serving_leg(duration_s: float, dev, streams: int = 16, rate_hz: float = 5.0,
                            id0=torch.from_numpy(pr.id0.astype(np.float32)).pin_memory(),
                            n0=torch.from_numpy(pr.n0.astype(np.float32)).pin_memory(),
                            st0=torch.from_numpy(pr.state).pin_memory()))
+    res_of = [pr.S * pr.P ** 2 * pr.F * iters for pr in pool]
     server = sgn.Server(16 << 30, max_slots=256, max_surfels_per_epoch=4_000_000)
 
     def submit(k, tag):
@@ -493,37 +531,10 @@ def serving_leg(duration_s: float, dev, streams: int = 16, rate_hz: float = 5.0,
         submit(k, 10_000_000 + k)
     server.drain()
     server.poll()
-    # open loop: merged Poisson schedule of the streams
-    rng = np.random.default_rng(7)
-    events = []
-    for st in range(streams):
-        t = rng.exponential(1.0 / rate_hz)
-        while t < duration_s:
-            events.append((t, st))
-            t += rng.exponential(1.0 / rate_hz)
-    events.sort()
-    base = server.stats()
-    done = []
-    t0 = time.perf_counter()
-    for i, (t, st) in enumerate(events):
-        now = time.perf_counter() - t0
-        if t > now:
-            time.sleep(t - now)
-        k = (st % 4) + (0 if st < streams // 2 else 4)  # half the streams at 640x480, half at 1280x720
-        submit(k, i + 1)
-        if i % 16 == 15:
-            done += server.poll()
-    server.drain()
-    done += server.poll()
-    lat = [c.latency_ms for c, _ in done if 1 <= c.tag <= len(events) and c.status == sgn.SGN_OK]
-    assert len(lat) == len(events), (len(lat), len(events))
-    stats = server.stats()
-    wall = time.perf_counter() - t0
-    res_open = stats["residuals"] - base["residuals"]
-    # saturated: the same request mix submitted at once, three bursts (host wall clock, which a
+    # saturated: the request mix submitted at once, three bursts (host wall clock, which a
     # descheduled host thread can stretch): the median burst
     sat_req = [(i % 8) for i in range(burst)]
-    res_burst = sum(pool[k].S * pool[k].P ** 2 * pool[k].F * iters for k in sat_req)
+    res_burst = sum(res_of[k] for k in sat_req)
     bursts = []
     for b in range(3):
         t1 = time.perf_counter()
@@ -533,6 +544,54 @@ def serving_leg(duration_s: float, dev, streams: int = 16, rate_hz: float = 5.0,
         bursts.append(time.perf_counter() - t1)
         server.poll()
     t_served = statistics.median(bursts)
+    sat = res_burst / t_served
+
+    def open_loop(rate_per_stream, seed, tag0):
+        """Merged Poisson schedule of the streams at rate_per_stream keyframes/s each, for duration_s."""
+        rng = np.random.default_rng(seed)
+        events = []
+        for st in range(streams):
+            t = rng.exponential(1.0 / rate_per_stream)
+            while t < duration_s:
+                events.append((t, st))
+                t += rng.exponential(1.0 / rate_per_stream)
+        events.sort()
+        base = server.stats()
+        done, lag = [], 0.0
+        t0 = time.perf_counter()
+        for i, (t, st) in enumerate(events):
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            else:
+                lag = max(lag, now - t)
+            k = (st % 4) + (0 if st < streams // 2 else 4)  # half the streams at 640x480, half at 1280x720
+            submit(k, tag0 + i)
+            if i % 16 == 15:
+                done += server.poll()
+        server.drain()
+        done += server.poll()
+        wall = time.perf_counter() - t0
+        mine = [c for c, _ in done if tag0 <= c.tag < tag0 + len(events) and c.status == sgn.SGN_OK]
+        assert len(mine) == len(events), (len(mine), len(events))
+        lat = np.array([c.latency_ms for c in mine])
+        qms = np.array([c.queue_ms for c in mine])
+        stats = server.stats()
+        offered = sum(res_of[(st % 4) + (0 if st < streams // 2 else 4)] for _, st in events) / duration_s
+        return {"rate_per_stream_hz": rate_per_stream, "requests": len(events), "duration_s": duration_s,
+                "offered_residuals_per_s": offered, "offered_fraction_of_saturated": offered / sat,
+                "served_residuals_per_s": (stats["residuals"] - base["residuals"]) / wall,
+                "epochs": int(stats["epochs"] - base["epochs"]),
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "max": float(lat.max()), "mean": float(lat.mean())},
+                "queue_ms": {"p50": float(np.percentile(qms, 50)), "p99": float(np.percentile(qms, 99))},
+                "p99_under_33ms": bool(np.percentile(lat, 99) < 33.0),
+                "max_submission_lag_s": lag}
+
+    mean_res = float(np.mean([res_of[(st % 4) + (0 if st < streams // 2 else 4)] for st in range(streams)]))
+    points = {"nominal": open_loop(rate_hz, 7, 30_000_000)}
+    for j, f in enumerate(loads):
+        points[f"load_{int(round(100 * f))}"] = open_loop(f * sat / mean_res / streams, 8 + j, 40_000_000 + 1_000_000 * j)
     server.close()
     # plain: one plan per keyframe size, upload + solve + readback per request, one stream
     stream = torch.cuda.Stream(device=dev)
@@ -567,13 +626,10 @@ def serving_leg(duration_s: float, dev, streams: int = 16, rate_hz: float = 5.0,
         t_plain = statistics.median(plain_runs)
         for pl in plans.values():
             pl._keep.clear()
-    lat = np.array(lat)
-    return {"streams": streams, "rate_per_stream_hz": rate_hz, "duration_s": duration_s, "requests": len(events),
-            "texels": "f16", "sizes": "half 640x480 (4800 surfels), half 1280x720 (14400 surfels); 8x8, 4 frames",
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max()), "mean": float(lat.mean())},
-            "offered_residuals_per_s": res_open / wall, "epochs": int(stats["epochs"] - base["epochs"]),
-            "saturated": {"requests": burst, "served_residuals_per_s": res_burst / t_served,
+    return {"streams": streams, "texels": "f16",
+            "sizes": "half 640x480 (4800 surfels), half 1280x720 (14400 surfels); 8x8, 4 frames",
+            "load_points": points,
+            "saturated": {"requests": burst, "served_residuals_per_s": sat,
                           "plain_residuals_per_s": res_burst / t_plain, "speedup": t_plain / t_served,
                           "burst_s": bursts, "plain_s": plain_runs,
                           "note": ("host-to-device uploads, frame prep, solve and device-to-host results included in "
@@ -742,31 +798,45 @@ def run_ours(args):
             stream.synchronize()
             return start.elapsed_time(end)
 
+        # the K-step region is timed repeatedly (at least 10 times and for at least --min-seconds of
+        # wall time, the same count on every rank); each repeat is bracketed by a barrier and takes the
+        # slowest rank's time; the headline is the median repeat, with the fastest and slowest beside it
         ranks.barrier()
         torch.cuda.synchronize()
+        first = ranks.max_ms(timed_steps(True))
+        repeats = int(ranks.max_ms(float(max(10, min(5000, -(-args.min_seconds * 1e3 // max(first, 1e-3)))))))
+        region_ms = []
         with ClockSampler(local) as clocks:
             time.sleep(0.3)
-            total_ms = timed_steps(True)
+            for _ in range(repeats):
+                ranks.barrier()
+                region_ms.append(ranks.max_ms(timed_steps(True)))
         torch.cuda.synchronize()
         ranks.barrier()
-        total_ms = ranks.max_ms(total_ms)
+        total_ms = statistics.median(region_ms)
         launches = launches_per_step * args.steps
         ranks.barrier()
-        one_ms = ranks.max_ms(timed_steps(False))
+        one_region_ms = []
+        for _ in range(max(3, repeats // 4)):
+            ranks.barrier()
+            one_region_ms.append(ranks.max_ms(timed_steps(False)))
+        one_ms = statistics.median(one_region_ms)
         ranks.barrier()
 
-        # (2) the Gauss-Newton kernel alone: the same K steps with the solve graph bracketed by events
-        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        for i in range(args.steps):
-            g_pre, g_gn, g_post = insts[i % R].split
-            g_pre.replay()
-            kev[i][0].record(stream)
-            g_gn.replay()
-            kev[i][1].record(stream)
-            g_post.replay()
-        stream.synchronize()
-        kern_ms = [a.elapsed_time(b) for a, b in kev]
+        # (2) the Gauss-Newton kernel alone: the same K steps with the solve graph bracketed by events,
+        # repeated until at least 200 launches are timed
+        kern_ms = []
+        for _ in range(max(1, -(-200 // args.steps))):
+            kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            for i in range(args.steps):
+                g_pre, g_gn, g_post = insts[i % R].split
+                g_pre.replay()
+                kev[i][0].record(stream)
+                g_gn.replay()
+                kev[i][1].record(stream)
+                g_post.replay()
+            stream.synchronize()
+            kern_ms += [a.elapsed_time(b) for a, b in kev]
 
         # (3) end to end through the C ABI from page-locked host buffers, results back on the host:
         # the K steps are enqueued back to back (each instance has its own host buffers), so the
@@ -798,15 +868,21 @@ def run_ours(args):
     value = ranks.throughput(res * args.steps, total_ms)
     peak, peak_kind = measured_peaks()
     kern_avg_s = statistics.mean(kern_ms) / 1e3
+    kq = statistics.quantiles(kern_ms, n=100)
     achieved = res * BYTES_PER_RESIDUAL[WORKLOAD["texels"]] / kern_avg_s / 1e9
     clk = clocks.summary()
     line = {
         "metric": "surfel-pixel GN residuals/s (640x480 keyframe solve)",
         "value": value, "unit": "residuals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "spread": {"repeats": len(region_ms), "value_min": ranks.throughput(res * args.steps, max(region_ms)),
+                   "value_max": ranks.throughput(res * args.steps, min(region_ms)),
+                   "ms_per_step_min": min(region_ms) / args.steps, "ms_per_step_max": max(region_ms) / args.steps,
+                   "note": "value = median over the repeats of the K-step region; min/max over the repeats"},
         "dtype": "f32", "data": "synthetic (seeded box-room renders, sigma 0.01 noise)",
         "one_stream": {"value": ranks.throughput(res * args.steps, one_ms), "ms_per_step": one_ms / args.steps,
-                       "note": "the same K graph replays one after another on one stream"},
+                       "repeats": len(one_region_ms),
+                       "note": "the same K graph replays one after another on one stream (median repeat)"},
         "config": {**WORKLOAD, "streams": len(streams), "l2": (f"inputs larger than L2: steps rotate over {R} keyframe instances "
                                       f"(~35 MB of traffic each, {R} x 35 MB vs 126 MB L2); no flush" if R * 35 > 2 * 126
                                       else f"NOT evicted from L2 ({R} instances of ~35 MB): profiling run only"),
@@ -825,6 +901,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "step_graphs": f"one CUDA graph replay per step (uploads + frame prep, solve, readback), plans alternating between {len(streams)} streams",
         "kernel_ms_per_step": statistics.mean(kern_ms),
+        "kernel_ms": {"launches": len(kern_ms), "mean": statistics.mean(kern_ms), "median": statistics.median(kern_ms),
+                      "min": min(kern_ms), "p99": kq[98], "max": max(kern_ms)},
         "clocks": clk,
     }
     if rank == 0 and not args.no_batch:
@@ -875,11 +953,15 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--min-seconds", type=float, default=4.0,
+                    help="repeat the K-step timed region for at least this much wall time (and at least 10 times)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-keyframe batched leg")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="duration of the serving leg (0 skips it)")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="duration of each open-loop serving run (nominal rate, 50 %% and 90 %% of the saturated "
+                         "throughput: three runs); 0 skips the serving leg")
     ap.add_argument("--instances", type=int, default=16, help="keyframe instances the steps rotate over (L2 eviction)")
     ap.add_argument("--streams", type=int, default=4, help="streams the keyframe instances alternate between")
     args = ap.parse_args()

@@ -42,7 +42,7 @@ extern "C" {
 #endif
 
 #define SGN_MAX_FRAMES 16
-#define SGN_ABI_VERSION 3
+#define SGN_ABI_VERSION 4
 
 typedef enum {
     SGN_OK = 0,
@@ -55,7 +55,17 @@ typedef enum {
     SGN_ERR_STATE = -7               /* call out of order (e.g. run before intrinsics/frames) */
 } sgn_status;
 
-typedef enum { SGN_F32 = 0, SGN_F16 = 1, SGN_BF16 = 2 } sgn_dtype;   /* frame texel storage */
+/* Frame texel storage (intensity I and central-difference gradient gx, gy of each pixel):
+ *   SGN_F32   16-byte texel, all three in FP32;
+ *   SGN_F16   8-byte texel, all three in FP16 (the gradient is the central difference of the FP16 image);
+ *   SGN_BF16  8-byte texel, all three in BF16 (likewise);
+ *   SGN_F16G  8-byte texel, gradient in FP16 and intensity in FP32 (the gradient is the central
+ *             difference of the FP32 image, rounded to FP16);
+ *   SGN_BF16G 8-byte texel, gradient in BF16 and intensity in FP32.
+ * The residual of Eq. 5 is a difference of intensities, so rounding the stored intensity moves the
+ * cost minimum itself, while a rounded gradient only perturbs the Jacobian (Eq. 8); the G formats
+ * keep the 8-byte texel of the reduced-precision formats with the intensity exact. */
+typedef enum { SGN_F32 = 0, SGN_F16 = 1, SGN_BF16 = 2, SGN_F16G = 3, SGN_BF16G = 4 } sgn_dtype;
 typedef enum { SGN_HOST = 0, SGN_DEVICE = 1 } sgn_mem;              /* where a pointer points */
 
 /* Surfel input states (sgn_init_surfels). */
@@ -115,9 +125,10 @@ sgn_status sgn_plan_num_surfels(const sgn_plan* plan, int* num_surfels);
 sgn_status sgn_plan_workspace_bytes(const sgn_plan* plan, size_t* bytes);
 
 /* Kernel mapping of sgn_run / sgn_solve: lanes per surfel (P=4: 8 or 16; P=8: 8, 16 or 32;
- * P=16: 32) and threads per block (multiple of 32 in [32, 256]); 0 selects the default
- * (P=4: 8, P=8: 16, P=16: 32 lanes; 256 threads).  Results do not depend on the mapping
- * beyond floating-point summation order. */
+ * P=16: 32) and threads per block (multiple of 32 in [32, 256], or 512 for square surfels with
+ * 4 pixels per lane (P=8 at 16 lanes), fixed damping and no staging: a block then solves an
+ * 8 x 4 square of tiles); 0 selects the default (P=4: 8, P=8: 16, P=16: 32 lanes; 256 threads).
+ * Results do not depend on the mapping beyond floating-point summation order. */
 sgn_status sgn_plan_set_mapping(sgn_plan* plan, int lanes_per_surfel, int block_threads);
 
 /* Bind a device workspace (>= sgn_plan_workspace_bytes, 256-byte aligned) and a CUDA stream
@@ -272,6 +283,7 @@ typedef struct {
     int cancelled;
     double latency_ms;   /* submission -> results in host memory */
     double queue_ms;     /* submission -> admission */
+    uint64_t admit_seq;  /* admission order (1, 2, ...); 0 if never admitted */
 } sgn_completion;
 
 typedef struct {
@@ -285,6 +297,9 @@ typedef struct {
  * of the requests in flight (admission by free memory): each admitted request takes its plan
  * workspace (sgn_plan_workspace_bytes) from the arena until it completes; a request larger than the
  * arena is refused at submission with SGN_ERR_ADMISSION, one that does not fit yet waits.
+ * Admission is first come, first served, except that later requests may pass one that does not
+ * fit yet; each waiting request is passed at most 8 times, after which nothing behind it is
+ * admitted until it fits (so no request waits indefinitely behind a stream of smaller ones).
  * compute_stream runs the batched solves, copy_stream the uploads, frame preparation and result
  * copies (two distinct non-default streams of the current device).  An epoch = one persistent batch
  * launch over every request uploaded since the previous launch, at most max_slots requests and

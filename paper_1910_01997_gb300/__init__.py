@@ -25,14 +25,14 @@ _lib = ctypes.CDLL(LIB_PATH)
 # ---------------------------------------------------------------------------------------- constants
 SGN_OK, SGN_ERR_INVALID_ARGUMENT, SGN_ERR_NOT_BOUND, SGN_ERR_WORKSPACE_TOO_SMALL = 0, -1, -2, -3
 SGN_ERR_CUDA, SGN_ERR_TIMEOUT, SGN_ERR_ADMISSION, SGN_ERR_STATE = -4, -5, -6, -7
-SGN_F32, SGN_F16, SGN_BF16 = 0, 1, 2
+SGN_F32, SGN_F16, SGN_BF16, SGN_F16G, SGN_BF16G = 0, 1, 2, 3, 4
 SGN_HOST, SGN_DEVICE = 0, 1
 SGN_STATE_EMPTY, SGN_STATE_VALID, SGN_STATE_TO_SEED = 0, 1, 2
 SGN_SURFEL_OK, SGN_SURFEL_EMPTY, SGN_SURFEL_UNSEEDED = 0, 1, 2
 SGN_SURFEL_UNDERDETERMINED, SGN_SURFEL_SINGULAR, SGN_SURFEL_STEP_REJECTED = 3, 4, 5
 SGN_SURFEL_SEEDED, SGN_SURFEL_FP64 = 0x40, 0x80
 SGN_MAX_FRAMES = 16
-DTYPES = {"f32": SGN_F32, "f16": SGN_F16, "bf16": SGN_BF16}
+DTYPES = {"f32": SGN_F32, "f16": SGN_F16, "bf16": SGN_BF16, "f16g": SGN_F16G, "bf16g": SGN_BF16G}
 
 
 class sgn_plan_desc(ctypes.Structure):
@@ -53,7 +53,7 @@ class sgn_request(ctypes.Structure):
 
 class sgn_completion(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int), ("cancelled", ctypes.c_int),
-                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double)]
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("admit_seq", ctypes.c_uint64)]
 
 
 class sgn_serving_stats(ctypes.Structure):

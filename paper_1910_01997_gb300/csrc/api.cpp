@@ -385,7 +385,7 @@ sgn_status sgn_plan_create(const sgn_plan_desc* d, sgn_plan** out) {
     if (d->width < d->patch || d->height < d->patch) return fail(SGN_ERR_INVALID_ARGUMENT, "image smaller than one tile");
     if (d->max_frames < 1 || d->max_frames > SGN_MAX_FRAMES)
         return fail(SGN_ERR_INVALID_ARGUMENT, "max_frames must be in [1, %d]", SGN_MAX_FRAMES);
-    if (d->image_dtype != SGN_F32 && d->image_dtype != SGN_F16 && d->image_dtype != SGN_BF16)
+    if (!(d->image_dtype >= SGN_F32 && d->image_dtype <= SGN_BF16G))
         return fail(SGN_ERR_INVALID_ARGUMENT, "unknown image dtype %d", int(d->image_dtype));
     if (!(d->huber_k > 0.0f) || !std::isfinite(d->huber_k)) return fail(SGN_ERR_INVALID_ARGUMENT, "huber_k must be positive and finite");
     if (!(d->lm_lambda >= 0.0f) || !std::isfinite(d->lm_lambda)) return fail(SGN_ERR_INVALID_ARGUMENT, "lm_lambda must be >= 0 and finite");
@@ -447,7 +447,12 @@ sgn_status sgn_plan_set_mapping(sgn_plan* p, int lanes_per_surfel, int block_thr
         return fail(SGN_ERR_INVALID_ARGUMENT, "circular surfels use 32 lanes per surfel");
     if (p->disc.empty() && !mapping_supported(p->desc.patch, G))
         return fail(SGN_ERR_INVALID_ARGUMENT, "%d lanes per surfel not supported for %dx%d tiles", G, p->desc.patch, p->desc.patch);
-    if (B < 32 || B > 256 || B % 32) return fail(SGN_ERR_INVALID_ARGUMENT, "block_threads must be a multiple of 32 in [32, 256]");
+    if (B == 512) {
+        if (!p->disc.empty() || p->desc.lm_adaptive || p->staging || G * 4 != p->desc.patch * p->desc.patch)
+            return fail(SGN_ERR_INVALID_ARGUMENT, "512-thread blocks need square surfels with 4 pixels per lane and fixed damping");
+    } else if (B < 32 || B > 256 || B % 32) {
+        return fail(SGN_ERR_INVALID_ARGUMENT, "block_threads must be a multiple of 32 in [32, 256], or 512");
+    }
     p->lanes = G;
     p->block = B;
     return SGN_OK;
@@ -456,6 +461,7 @@ sgn_status sgn_plan_set_mapping(sgn_plan* p, int lanes_per_surfel, int block_thr
 sgn_status sgn_plan_set_staging(sgn_plan* p, int enabled) {
     if (!p) return fail(SGN_ERR_INVALID_ARGUMENT, "plan is NULL");
     if (enabled != 0 && enabled != 1) return fail(SGN_ERR_INVALID_ARGUMENT, "enabled must be 0 or 1");
+    if (enabled && p->block > 256) return fail(SGN_ERR_INVALID_ARGUMENT, "staging needs blocks of at most 256 threads");
     p->staging = enabled != 0;
     return SGN_OK;
 }

@@ -80,23 +80,24 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_gn_batch(const PlanParams* _
             case SGN_F32: dispatch_patch<V, SGN_F32>(my, w, lane, iters, wref, group_words); break;
             case SGN_F16: dispatch_patch<V, SGN_F16>(my, w, lane, iters, wref, group_words); break;
             case SGN_BF16: dispatch_patch<V, SGN_BF16>(my, w, lane, iters, wref, group_words); break;
+            case SGN_F16G: dispatch_patch<V, SGN_F16G>(my, w, lane, iters, wref, group_words); break;
+            case SGN_BF16G: dispatch_patch<V, SGN_BF16G>(my, w, lane, iters, wref, group_words); break;
             default: break;
         }
     }
 }
 
-static cudaError_t batch_attributes() {
-    static bool done = false;  // same values from every thread: a benign race
-    if (done) return cudaSuccess;
-    const int max_bytes = batch_scratch_bytes(kMaxFrames);
-    cudaError_t e = cudaFuncSetAttribute(k_gn_batch<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gn_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    if (e == cudaSuccess) done = true;
-    return e;
+LaunchAttrs g_batch_attrs[2];
+
+// Dynamic shared-memory limit and carveout of variant V on the current device for max_frames.
+static cudaError_t batch_attributes(int variant, int max_frames) {
+    const int smem = batch_scratch_bytes(max_frames), max_bytes = batch_scratch_bytes(kMaxFrames);
+    return variant == 0 ? configure_launch(k_gn_batch<0>, g_batch_attrs[0], max_bytes, smem, 2)
+                        : configure_launch(k_gn_batch<1>, g_batch_attrs[1], max_bytes, smem, 2);
 }
 
 int batch_blocks_per_sm(int variant, int block_threads, int max_frames) {
-    if (batch_attributes() != cudaSuccess) return 0;
+    if (max_frames < 1 || max_frames > kMaxFrames || batch_attributes(variant, max_frames) != cudaSuccess) return 0;
     int n = 0;
     const size_t smem = batch_scratch_bytes(max_frames);
     cudaError_t e = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gn_batch<0>, block_threads, smem)
@@ -108,14 +109,11 @@ int launch_gn_batch(const PlanParams* d_plans, const WorkItem* d_items, int n_it
                     int variant, int grid, int block_threads, int max_frames, void* stream) {
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (block_threads != kBatchBlock || max_frames < 1 || max_frames > kMaxFrames) return int(cudaErrorInvalidConfiguration);
-    cudaError_t e = batch_attributes();
+    cudaError_t e = batch_attributes(variant, max_frames);
     if (e != cudaSuccess) return int(e);
     e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return int(e);
     const size_t smem = batch_scratch_bytes(max_frames);
-    static int carveout[2] = {-1, -1};
-    e = variant == 0 ? prefer_l1(k_gn_batch<0>, int(smem), 2, carveout[0]) : prefer_l1(k_gn_batch<1>, int(smem), 2, carveout[1]);
-    if (e != cudaSuccess) return int(e);
     if (variant == 0)
         k_gn_batch<0><<<grid, block_threads, smem, st>>>(d_plans, d_items, n_items, d_counter, iters, max_frames);
     else

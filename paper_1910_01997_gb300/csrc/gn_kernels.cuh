@@ -32,8 +32,11 @@ __device__ __forceinline__ int block_surfel(const PlanParams& pp, int G) {
     return s < 0 ? pp.S : s;
 }
 
-template <int P, int G, int DT, bool LMA = false>
-__global__ void __launch_bounds__(256, gn_min_blocks(P, G)) k_gn(const __grid_constant__ PlanParams pp, int iters, int mode) {
+// BT: most threads per block.  256-thread blocks take a 4 x 4 square of tiles (16 groups of 16 lanes);
+// a 512-thread block takes 8 x 4 tiles, the share of one SM at 640x480 (4800 surfels on 152 SMs),
+// whose texel footprint per frame is smaller than that of two separate 4 x 4 squares.
+template <int P, int G, int DT, bool LMA = false, int BT = 256>
+__global__ void __launch_bounds__(BT, BT > 256 ? 1 : gn_min_blocks(P, G)) k_gn(const __grid_constant__ PlanParams pp, int iters, int mode) {
     __shared__ PlanParams spp;
     extern __shared__ float4 sdyn[];
     load_plan(&spp, &pp);
@@ -83,17 +86,11 @@ __global__ void __launch_bounds__(256, 2) k_gn_disc(const __grid_constant__ Plan
 
 template <int P, int DT, int DPPL>
 int launch_disc(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st) {
-    static bool attr_set = false;  // same value from every thread: a benign race
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(k_gn_disc<P, DT, DPPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   scratch_bytes(8, kMaxFrames));
-        if (e != cudaSuccess) return int(e);
-        attr_set = true;
-    }
-    static int carveout = -1;
-    const cudaError_t e = prefer_l1(k_gn_disc<P, DT, DPPL>, scratch_bytes(block / 32, pp.F), 2 * 256 / block, carveout);
+    static LaunchAttrs attrs;
+    const int smem = scratch_bytes(block / 32, pp.F);
+    const cudaError_t e = configure_launch(k_gn_disc<P, DT, DPPL>, attrs, scratch_bytes(8, kMaxFrames), smem, 2 * 256 / block);
     if (e != cudaSuccess) return int(e);
-    k_gn_disc<P, DT, DPPL><<<grid, block, scratch_bytes(block / 32, pp.F), st>>>(pp, iters, mode);
+    k_gn_disc<P, DT, DPPL><<<grid, block, smem, st>>>(pp, iters, mode);
     return int(cudaGetLastError());
 }
 
@@ -106,46 +103,33 @@ int launch_disc_ppl(const PlanParams& pp, int iters, int mode, int grid, int blo
     return int(cudaErrorInvalidConfiguration);
 }
 
+// Plain launch of one Gauss-Newton kernel instantiation (direct gathers).
+template <int P, int G, int DT, bool LMA, int BT>
+int launch_plain(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st) {
+    static LaunchAttrs attrs;
+    const int smem = scratch_bytes(block / G, pp.F);
+    const int blocks = BT > 256 ? 1 : gn_min_blocks(P, G) * 256 / block;
+    const cudaError_t e = configure_launch(k_gn<P, G, DT, LMA, BT>, attrs, scratch_bytes(BT / G, kMaxFrames), smem, blocks);
+    if (e != cudaSuccess) return int(e);
+    k_gn<P, G, DT, LMA, BT><<<grid, block, smem, st>>>(pp, iters, mode);
+    return int(cudaGetLastError());
+}
+
 template <int P, int G, int DT>
 int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, cudaStream_t st, const void* tmap) {
-    const int scratch = scratch_bytes(block / G, pp.F);
-    if (pp.lm_adaptive) {  // Marquardt schedule: its own instantiation (direct gathers)
-        static bool attr_set = false;  // same value from every thread: a benign race
-        if (!attr_set) {
-            const cudaError_t e = cudaFuncSetAttribute(k_gn<P, G, DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       scratch_bytes(256 / G, kMaxFrames));
-            if (e != cudaSuccess) return int(e);
-            attr_set = true;
-        }
-        static int carveout = -1;
-        const cudaError_t e = prefer_l1(k_gn<P, G, DT, true>, scratch, gn_min_blocks(P, G) * 256 / block, carveout);
-        if (e != cudaSuccess) return int(e);
-        k_gn<P, G, DT, true><<<grid, block, scratch, st>>>(pp, iters, mode);
-        return int(cudaGetLastError());
+    if (pp.lm_adaptive) return launch_plain<P, G, DT, true, 256>(pp, iters, mode, grid, block, st);  // Marquardt schedule
+    if (!tmap && block > 256) {
+        if constexpr (P * P / G == 4) return launch_plain<P, G, DT, false, 512>(pp, iters, mode, grid, block, st);
+        return int(cudaErrorInvalidConfiguration);
     }
-    if (!tmap) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            const cudaError_t e = cudaFuncSetAttribute(k_gn<P, G, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       scratch_bytes(256 / G, kMaxFrames));
-            if (e != cudaSuccess) return int(e);
-            attr_set = true;
-        }
-        static int carveout = -1;
-        const cudaError_t e = prefer_l1(k_gn<P, G, DT>, scratch, gn_min_blocks(P, G) * 256 / block, carveout);
-        if (e != cudaSuccess) return int(e);
-        k_gn<P, G, DT><<<grid, block, scratch, st>>>(pp, iters, mode);
-        return int(cudaGetLastError());
-    }
-    // boxes of the block's groups after the scratch, plus slack to align them to 128 bytes
-    const int smem = scratch + (block / G) * kStageSlots * box_stride(P, DT) + 128;
-    static bool attr_set = false;
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(k_gn_staged<P, G, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   scratch_bytes(256 / G, kMaxFrames) + (256 / G) * kStageSlots * box_stride(P, DT) + 128);
-        if (e != cudaSuccess) return int(e);
-        attr_set = true;
-    }
+    if (!tmap) return launch_plain<P, G, DT, false, 256>(pp, iters, mode, grid, block, st);
+    // staged: boxes of the block's groups after the scratch, plus slack to align them to 128 bytes
+    static LaunchAttrs attrs;
+    const int boxes = kStageSlots * box_stride(P, DT);
+    const int smem = scratch_bytes(block / G, pp.F) + (block / G) * boxes + 128;
+    const cudaError_t e = configure_launch(k_gn_staged<P, G, DT>, attrs, scratch_bytes(256 / G, kMaxFrames) + (256 / G) * boxes + 128,
+                                           smem, gn_min_blocks(P, G) * 256 / block);
+    if (e != cudaSuccess) return int(e);
     TexMap m;
     memcpy(&m, tmap, sizeof m);
     k_gn_staged<P, G, DT><<<grid, block, smem, st>>>(pp, iters, mode, m);
@@ -155,7 +139,8 @@ int launch_one(const PlanParams& pp, int iters, int mode, int grid, int block, c
 template <int DT>
 int launch_gn_dtype(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap) {
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (block > 256 || block % G) return int(cudaErrorInvalidConfiguration);
+    if (block > 512 || block % G || (block > 256 && (block != 512 || tmap || pp.lm_adaptive || pp.disc_n > 0)))
+        return int(cudaErrorInvalidConfiguration);
     const int grid = pp.S > 0 ? square_blocks(pp.TX, pp.TY, block / G) : 0;
     if (grid == 0) return cudaSuccess;
     if (pp.disc_n > 0) {  // circular surfels: 32 lanes per surfel, no staging

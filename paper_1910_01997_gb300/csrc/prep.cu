@@ -16,6 +16,8 @@ namespace sgn {
 int launch_gn_f32(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap);
 int launch_gn_f16(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap);
 int launch_gn_bf16(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap);
+int launch_gn_f16g(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap);
+int launch_gn_bf16g(const PlanParams& pp, int iters, int mode, int G, int block, void* stream, const void* tmap);
 
 int launch_gn(const PlanParams& pp, int iters, int mode, int lanes_per_surfel, int block_threads, void* stream,
               const void* tmap) {
@@ -23,6 +25,8 @@ int launch_gn(const PlanParams& pp, int iters, int mode, int lanes_per_surfel, i
         case SGN_F32: return launch_gn_f32(pp, iters, mode, lanes_per_surfel, block_threads, stream, tmap);
         case SGN_F16: return launch_gn_f16(pp, iters, mode, lanes_per_surfel, block_threads, stream, tmap);
         case SGN_BF16: return launch_gn_bf16(pp, iters, mode, lanes_per_surfel, block_threads, stream, tmap);
+        case SGN_F16G: return launch_gn_f16g(pp, iters, mode, lanes_per_surfel, block_threads, stream, tmap);
+        case SGN_BF16G: return launch_gn_bf16g(pp, iters, mode, lanes_per_surfel, block_threads, stream, tmap);
         default: return int(cudaErrorInvalidValue);
     }
 }
@@ -86,7 +90,8 @@ struct PrepArgs {
     int W, H, first, dtype;
 };
 
-// Intensity as stored in the texel type (FP32, or rounded to FP16 / BF16).
+// Intensity as stored in the texel type (FP32 in SGN_F32, SGN_F16G and SGN_BF16G; rounded to FP16 / BF16
+// in SGN_F16 / SGN_BF16).
 __device__ __forceinline__ float stored(float v, int dtype) {
     if (dtype == SGN_F16) return __half2float(__float2half_rn(v));
     if (dtype == SGN_BF16) return __bfloat162float(__float2bfloat16_rn(v));
@@ -94,9 +99,12 @@ __device__ __forceinline__ float stored(float v, int dtype) {
 }
 
 // Intensity + central-difference gradient (the grad I of Eq. 8), packed as one texel per pixel:
-// (gx, gy, I, 0).  The gradient is taken from the intensities as stored, so that with FP16/BF16
-// texels it is the exact central difference of the stored image (half the difference of two values
-// on the storage grid fits the storage mantissa).  Border rows/columns get a zero gradient; the
+// (gx, gy, I, I(x + 1, y)) in FP32 (the right neighbour's intensity fills the fourth word, so that a
+// bilinear sample blends intensity pairs; 0 past the last column), (gx, gy, I, 0) in FP16/BF16, or
+// (gx, gy) then I for the G formats.  The gradient is taken from the intensities
+// as stored, so that with FP16/BF16 texels it is the exact central difference of the stored image
+// (half the difference of two values on the storage grid fits the storage mantissa); the G formats
+// round the FP32 central difference to their gradient type.  Border rows/columns get a zero gradient; the
 // validity rule of the warp never samples them.
 __global__ void __launch_bounds__(256) k_prep_frames(const __grid_constant__ PrepArgs a) {
     const int f = blockIdx.z;
@@ -111,19 +119,26 @@ __global__ void __launch_bounds__(256) k_prep_frames(const __grid_constant__ Pre
     const float gy = (y >= 1 && y <= a.H - 2) ? 0.5f * (stored(__ldg(row + x + sp), dt) - stored(__ldg(row + x - sp), dt)) : 0.0f;
     const long long o = (long long)(a.first + f) * a.plane + (long long)y * a.tex_pitch + x;
     if (a.dtype == SGN_F32) {
-        static_cast<float4*>(a.dst)[o] = make_float4(gx, gy, I, 0.0f);
+        const float Ir = x + 1 < a.W ? __ldg(row + x + 1) : 0.0f;
+        static_cast<float4*>(a.dst)[o] = make_float4(gx, gy, I, Ir);
     } else if (a.dtype == SGN_F16) {
         __half2 lo = __floats2half2_rn(gx, gy), hi = __floats2half2_rn(I, 0.0f);
         uint2 v;
         v.x = *reinterpret_cast<unsigned*>(&lo);
         v.y = *reinterpret_cast<unsigned*>(&hi);
         static_cast<uint2*>(a.dst)[o] = v;
-    } else {
+    } else if (a.dtype == SGN_BF16) {
         __nv_bfloat162 lo = __floats2bfloat162_rn(gx, gy), hi = __floats2bfloat162_rn(I, 0.0f);
         uint2 v;
         v.x = *reinterpret_cast<unsigned*>(&lo);
         v.y = *reinterpret_cast<unsigned*>(&hi);
         static_cast<uint2*>(a.dst)[o] = v;
+    } else if (a.dtype == SGN_F16G) {
+        __half2 g = __floats2half2_rn(gx, gy);
+        static_cast<uint2*>(a.dst)[o] = make_uint2(*reinterpret_cast<unsigned*>(&g), __float_as_uint(I));
+    } else {
+        __nv_bfloat162 g = __floats2bfloat162_rn(gx, gy);
+        static_cast<uint2*>(a.dst)[o] = make_uint2(*reinterpret_cast<unsigned*>(&g), __float_as_uint(I));
     }
 }
 

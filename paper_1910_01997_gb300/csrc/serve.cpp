@@ -100,7 +100,14 @@ struct Job {
     int epoch = -1;
     Clock::time_point t_submit, t_admit;
     sgn_status result = SGN_OK;
+    int overtaken = 0;       // later requests admitted while this one waited for arena memory
+    uint64_t admit_seq = 0;  // admission order (1, 2, ...); 0 until admitted
 };
+
+// A request that does not fit the free arena yet lets at most this many later requests pass it;
+// then nothing behind it is admitted until it fits (the requests in flight finish and free their
+// memory), so that a large request cannot be starved by a stream of small ones.
+constexpr int kMaxOvertake = 8;
 
 struct Epoch {
     std::vector<Job*> jobs;
@@ -123,6 +130,7 @@ struct sgn_server {
     size_t table_bytes = 0;
     int max_items = 0;
     int sms = 0;  // multiprocessors of the device (the launch grid is sms x resident blocks)
+    uint64_t admitted = 0;  // requests admitted so far (server thread)
     bool table_busy[2] = {false, false};
     std::vector<sgn::PlanParams> h_plans;
     std::vector<sgn::WorkItem> h_items;
@@ -177,6 +185,7 @@ void finish_job(sgn_server* s, Job* j, sgn_status st) {
         c.status = j->cancelled ? SGN_ERR_STATE : st;
         c.latency_ms = lat;
         c.queue_ms = ms_between(j->t_submit, j->t_admit.time_since_epoch().count() ? j->t_admit : now);
+        c.admit_seq = j->admit_seq;
         c.cancelled = j->cancelled ? 1 : 0;
         s->completed.push_back(c);
         if (!j->cancelled && st == SGN_OK) {
@@ -314,15 +323,23 @@ void server_loop(sgn_server* s) {
                 ++it;
             }
         }
-        // admission: FIFO, later requests may pass one that does not fit yet
+        // admission: FIFO; a later request may pass one that does not fit yet, at most kMaxOvertake
+        // times per waiting request, after which admission stops at that request until it fits
+        std::vector<Job*> waiting;
         for (auto it = s->queued.begin(); it != s->queued.end();) {
             Job* j = *it;
             if (!s->arena.alloc(j->bytes, &j->off)) {
-                std::lock_guard<std::mutex> lk(s->mu);
-                s->admission_waits++;
+                {
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    s->admission_waits++;
+                }
+                if (j->overtaken >= kMaxOvertake) break;
+                waiting.push_back(j);
                 ++it;
                 continue;
             }
+            for (Job* w : waiting) ++w->overtaken;
+            j->admit_seq = ++s->admitted;
             j->t_admit = Clock::now();
             sgn_status st = start_upload(s, j);
             it = s->queued.erase(it);

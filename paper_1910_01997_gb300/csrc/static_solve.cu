@@ -57,13 +57,15 @@ sgn_status scratch_address(int dev, void** out) {
     return SGN_OK;
 }
 
-bool on_device(const void* p) {
+// Can the kernels, running on device `dev`, use p directly?  Memory of device `dev` or managed
+// memory; another GPU's memory is refused (the kernels would need peer access to it).
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
 }
 
 bool is_rotation(const double* T) {
@@ -94,7 +96,7 @@ extern "C" sgn_status sgn_solve_static(const sgn_plan_desc* d, const double intr
     if (d->patch != 4 && d->patch != 8 && d->patch != 16) return error(SGN_ERR_INVALID_ARGUMENT, "patch must be 4, 8 or 16");
     if (d->width < 8 || d->height < 8 || d->width > 16384 || d->height > 16384 || d->width < d->patch || d->height < d->patch)
         return error(SGN_ERR_INVALID_ARGUMENT, "image size %dx%d not supported", d->width, d->height);
-    if (d->image_dtype != SGN_F32 && d->image_dtype != SGN_F16 && d->image_dtype != SGN_BF16)
+    if (!(d->image_dtype >= SGN_F32 && d->image_dtype <= SGN_BF16G))
         return error(SGN_ERR_INVALID_ARGUMENT, "unknown image dtype");
     if (!(d->huber_k > 0.0f) || !std::isfinite(d->huber_k) || !(d->lm_lambda >= 0.0f) || !std::isfinite(d->lm_lambda) ||
         std::isnan(d->fp64_cond) || (d->optimize_normal != 0 && d->optimize_normal != 1) || d->min_residuals < 0 ||
@@ -121,15 +123,15 @@ extern "C" sgn_status sgn_solve_static(const sgn_plan_desc* d, const double intr
         return error(SGN_ERR_WORKSPACE_TOO_SMALL,
                      "%d frames of %dx%d texels need %zu bytes; the static scratch holds %u (use a plan with a workspace)",
                      F, W, H, need, unsigned(SGN_STATIC_SCRATCH_BYTES));
-    for (const void* p : dev_ptrs)
-        if (!on_device(p)) return error(SGN_ERR_INVALID_ARGUMENT, "inputs and outputs must be device memory");
-    for (int f = 0; f < F; ++f)
-        if (!on_device(frames[f])) return error(SGN_ERR_INVALID_ARGUMENT, "frame %d is not device memory", f);
-
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return error(SGN_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return error(SGN_ERR_INVALID_ARGUMENT, "device ordinal %d not supported", dev);
+    for (const void* p : dev_ptrs)
+        if (!on_device(p, dev))
+            return error(SGN_ERR_INVALID_ARGUMENT, "inputs and outputs must be memory of the current device (%d)", dev);
+    for (int f = 0; f < F; ++f)
+        if (!on_device(frames[f], dev)) return error(SGN_ERR_INVALID_ARGUMENT, "frame %d is not memory of the current device", f);
     void* scratch = nullptr;
     sgn_status st = scratch_address(dev, &scratch);
     if (st != SGN_OK) return st;

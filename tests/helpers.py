@@ -45,6 +45,13 @@ def oracle_solve(prob, iters, **opts):
     return out
 
 
+# The FP32 rounding scale of the kernel's inputs: the GPU starts from float32(id0), float32(n0), a
+# relative change of at most 2^-24 per value; the stability test perturbs the oracle's initial values
+# by twice that (one FP32 ulp, relative).  The FP32 error of each later step is covered separately
+# by the path x condition-number criterion of oracle_stable.
+FP32_INPUT_EPS = 2.0 ** -23
+
+
 def round_bf16(x):
     """Round float32 values to bfloat16 (nearest, ties to even) and back, in numpy."""
     b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
@@ -61,6 +68,9 @@ def quantize(frames, dtype):
 
 
 MANTISSA_BITS = {"f32": 23, "f16": 10, "bf16": 7}
+# Texel formats: the type their intensity and their gradient are stored in.
+INTENSITY_TYPE = {"f32": "f32", "f16": "f16", "bf16": "bf16", "f16g": "f32", "bf16g": "f32"}
+GRADIENT_TYPE = {"f32": "f32", "f16": "f16", "bf16": "bf16", "f16g": "f16", "bf16g": "bf16"}
 
 
 def ulp(x, dtype):
@@ -71,15 +81,17 @@ def ulp(x, dtype):
 
 
 def stored_planes(frames, dtype):
-    """Intensity and central-difference gradient planes as a texel type stores them: intensities
-    rounded to the type, gradients as half differences of the rounded intensities (exact in FP32)
-    rounded to the type, zero on the border rows/columns.  Computed here in numpy from the inputs."""
-    Iq = quantize(frames, dtype).astype(np.float32)
+    """Intensity and central-difference gradient planes as a texel format stores them: intensities
+    in the format's intensity type, gradients as half differences of the stored intensities (in
+    FP32, where they are exact for FP16/BF16 intensities) rounded to the format's gradient type,
+    zero on the border rows/columns.  Computed here in numpy from the inputs."""
+    Iq = quantize(frames, INTENSITY_TYPE[dtype]).astype(np.float32)
     gx = np.zeros_like(Iq)
     gy = np.zeros_like(Iq)
     gx[:, :, 1:-1] = np.float32(0.5) * (Iq[:, :, 2:] - Iq[:, :, :-2])
     gy[:, 1:-1, :] = np.float32(0.5) * (Iq[:, 2:, :] - Iq[:, :-2, :])
-    return tuple(quantize(a, dtype).astype(np.float64) for a in (Iq, gx, gy))
+    gt = GRADIENT_TYPE[dtype]
+    return Iq.astype(np.float64), quantize(gx, gt).astype(np.float64), quantize(gy, gt).astype(np.float64)
 
 
 def oracle_solve_planes(prob, planes, iters, **opts):
@@ -89,14 +101,17 @@ def oracle_solve_planes(prob, planes, iters, **opts):
     return out
 
 
-def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=3e-5, seeds=(1, 2, 3), planes=None,
-                  **opts):
+def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=FP32_INPUT_EPS, seeds=(1, 2, 3),
+                  planes=None, step_seeds=(11, 12), **opts):
     """Surfels whose oracle result after `iters` iterations is a stable function of the inputs.
 
-    The oracle alone is re-run with the initial parameters perturbed by a relative eps and the frame
-    data perturbed at the rounding scale of the texel type (uniform +-ulp/2 per pixel for each seed;
-    for FP32 +-2 ulp, standing for the FP32 arithmetic of a sample), plus, for FP16/BF16, once on
-    the intensity and gradient planes as that type stores them.  With `planes` (intensity and gradient planes given to the
+    The oracle alone is re-run with the initial parameters perturbed by a relative eps (default: one
+    FP32 ulp, the rounding the GPU's inputs undergo) and the frame data perturbed at the rounding
+    scale of the format's intensity type (uniform +-ulp/2 per pixel for each seed; for FP32 +-2 ulp,
+    standing for the FP32 arithmetic of a sample), plus, for the reduced-precision formats, once on
+    the intensity and gradient planes as that format stores them; and, with step_seeds, re-run one
+    iteration at a time with its parameters rounded to FP32 and perturbed by FP32_STEP_EPS (relative)
+    after every iteration.  With `planes` (intensity and gradient planes given to the
     oracle) those planes are perturbed by +-2 FP32 ulp.  A surfel is stable when every re-run keeps
     its status and stays within half the tolerance of the unperturbed result, and when the path its
     parameters travel over the iterations, times the condition number of its scaled normal
@@ -116,8 +131,9 @@ def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=3e-5, 
             problems.append((k, oracle.Problem.from_planes(prob.W, prob.H, prob.P, prob.cam, prob.keyframe, *pl,
                                                            prob.poses)))
         else:
-            scale = 2.0 if dtype == "f32" else 0.5
-            frames = prob.frames + scale * ulp(prob.frames, dtype) * rng.uniform(-1, 1, prob.frames.shape)
+            itype = INTENSITY_TYPE[dtype]
+            scale = 2.0 if itype == "f32" else 0.5
+            frames = prob.frames + scale * ulp(prob.frames, itype) * rng.uniform(-1, 1, prob.frames.shape)
             problems.append((k, oracle.Problem(prob.W, prob.H, prob.P, prob.cam, prob.keyframe, frames, prob.poses)))
     if planes is None and dtype != "f32":
         problems.append((99, oracle.Problem.from_planes(prob.W, prob.H, prob.P, prob.cam, prob.keyframe,
@@ -131,7 +147,57 @@ def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=3e-5, 
         stable &= (p["status"] == base["status"])
         stable &= np.abs(p["id"] / np.where(base["id"] != 0, base["id"], 1.0) - 1.0) <= 0.5 * tol_depth
         stable &= angle_deg(p["n"], base["n"]) <= 0.5 * tol_deg
+    if step_seeds and not prm.lm_adaptive:
+        # the parameters perturbed after every iteration (the rounding of the GPU's FP32 state)
+        if planes is not None:
+            ob = oracle.Problem.from_planes(prob.W, prob.H, prob.P, prob.cam, prob.keyframe, *planes, prob.poses)
+        else:
+            ob = oracle.Problem.from_synth(prob)
+        for k in step_seeds:
+            p = oracle_perturbed_steps(ob, prm, iters, prob.id0, prob.n0, prob.state, np.random.default_rng([k, 79]),
+                                       FP32_STEP_EPS)
+            # each iteration's FP32 sums (relative error ~1e-6) move its step by up to that much
+            # times the scaled condition number of the iteration's normal equations
+            stable &= (p["step_err_n"] * 1e-6 <= 0.5 * tol_deg) & (p["step_err_id"] * 1e-6 <= 0.5 * tol_depth)
+            stable &= (p["status"] == base["status"])
+            stable &= np.abs(p["id"] / np.where(base["id"] != 0, base["id"], 1.0) - 1.0) <= 0.5 * tol_depth
+            stable &= angle_deg(p["n"], base["n"]) <= 0.5 * tol_deg
     return stable
+
+
+# Relative perturbation of the parameters after every iteration in the stability re-runs: the GPU keeps
+# id_s and n in FP32, so each update rounds them (half an ulp) on top of the FP32 error of the step
+# itself (a few ulps); two ulps stand for both.
+FP32_STEP_EPS = 2.0 ** -22
+
+
+def oracle_perturbed_steps(ob, prm, iters, id0, n0, state, rng, rel):
+    """The oracle's seeding and Gauss-Newton iterations one at a time, with the parameters rounded to
+    FP32 and multiplied by (1 + rel u), u uniform in [-1, 1], after every iteration (the normal
+    renormalised): the oracle's result under a per-iteration perturbation at the FP32 rounding scale.
+    Also returns, per surfel, the sum over the iterations of each step's size (normal rotation in
+    degrees, relative inverse-depth change) times the scaled condition number of that iteration's
+    normal equations ("step_err_n", "step_err_id"): the first-order growth of an FP32 relative error
+    in the sums of one iteration through its solve."""
+    id_s, n, status = ob.seed(id0, n0, state)
+    p = None
+    err_n, err_id = np.zeros(len(id_s)), np.zeros(len(id_s))
+    for _ in range(iters):
+        p = ob.gauss_newton(prm, 1, id_s, n, status, diagnostics=True)
+        kap = scaled_cond(p["H_last"]) if prm.optimize_normal else np.ones(len(id_s))
+        with np.errstate(invalid="ignore"):
+            err_n += np.nan_to_num(p["path_n"] * kap, nan=np.inf)
+            err_id += np.nan_to_num(p["path_id"] * kap, nan=np.inf)
+        id_s = p["id"].astype(np.float32).astype(np.float64) * (1.0 + rel * rng.uniform(-1, 1, len(p["id"])))
+        n = p["n"].astype(np.float32).astype(np.float64) * (1.0 + rel * rng.uniform(-1, 1, p["n"].shape))
+        n /= np.maximum(np.linalg.norm(n, axis=1, keepdims=True), 1e-30)
+        status = p["status"]
+    if p is None:
+        p = ob.gauss_newton(prm, 0, id_s, n, status, diagnostics=False)
+    else:  # parameters of the last iteration, unperturbed
+        p = ob.gauss_newton(prm, 0, p["id"], p["n"], p["status"], diagnostics=False)
+    p["step_err_n"], p["step_err_id"] = err_n, err_id
+    return p
 
 
 def scaled_cond(H6):

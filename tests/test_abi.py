@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(sgn):
 def test_library_has_no_dynamic_cuda_runtime_dependency(sgn):
     # statically linked cudart: the library loads on hosts without a CUDA runtime in the loader path
     ctypes.CDLL(sgn.LIB_PATH)
-    assert sgn.sgn_abi_version() == 3
+    assert sgn.sgn_abi_version() == 4
 
 
 def test_desc_defaults_and_validation(sgn):
@@ -155,4 +155,4 @@ def test_transfer_and_render_argument_checks(sgn):
     for radius in (0.0, -2.0, float("nan"), 2000.0):
         assert render(cam, 160, 120, 1, radius, p) == sgn.SGN_ERR_INVALID_ARGUMENT
     assert render(cam, 160, 120, 1, 3.0, p) == sgn.SGN_ERR_INVALID_ARGUMENT  # host memory
-    assert lib.sgn_abi_version() == 3
+    assert lib.sgn_abi_version() == 4

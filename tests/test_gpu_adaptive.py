@@ -19,7 +19,7 @@ def test_adaptive_parity_full_size():
     decided = o["decision_margin"] > 1e-4
     print("decision margin below 1e-4:", int((~decided).sum()), "of", prob.S)
     # (about 40 % of surfels decide within that margin; parity is defined on the others)
-    _check(prob, g, o, "f32", "adaptive LM", 10, also_stable=decided, min_frac=0.1, lm_adaptive=True)
+    _check(prob, g, o, "f32", "adaptive LM", 10, frac="adaptive", also_stable=decided, lm_adaptive=True)
 
 
 def test_adaptive_never_raises_the_mean_cost():

@@ -148,5 +148,5 @@ def test_all_solves_in_fp64_match_oracle():
     print("all-FP64", {k: v for k, v in st.items() if k not in ("rel", "ang", "mask", "stable")})
     ok = (g["status"] & 0x3F) == 0
     assert ((g["status"][ok] & FP64_FLAG) != 0).mean() > 0.99
-    assert st["n"] >= TOL["well_posed"]["min_stable_frac"]["f32"] * st["n_usable"]
+    assert st["n"] >= TOL["well_posed"]["min_stable_frac"]["room"] * st["n_usable"]
     assert st["depth_max"] <= tol["depth_rel"] and st["ang_max"] <= tol["normal_deg"], (st["depth_max"], st["ang_max"])

@@ -110,3 +110,36 @@ def test_cancel_and_drain_deadline():
     assert done[3][0].cancelled == 1 and done[3][0].status == sgn.SGN_ERR_STATE
     assert done[1][0].status == sgn.SGN_OK and done[2][0].status == sgn.SGN_OK
     server.close()
+
+
+def test_large_request_is_not_starved_by_small_ones():
+    """A request that does not fit the free arena is passed by at most 8 later requests; then
+    admission waits for it, however many small requests keep arriving."""
+    import paper_1910_01997_gb300 as sgn
+
+    small = synth.room_problem(50, W=320, H=240, F=2)
+    big = synth.room_problem(51, W=640, H=480, F=4)
+
+    def ws(p):
+        h = sgn.sgn_plan_create(sgn.sgn_plan_desc_default(p.W, p.H, p.P, p.F))
+        try:
+            return sgn.sgn_plan_workspace_bytes(h)
+        finally:
+            sgn.sgn_plan_destroy(h)
+
+    # the big request fits only while at most a few small ones hold arena memory
+    arena = ws(big) + ws(small) // 2 + (1 << 20)
+    server = sgn.Server(arena)
+    for t in range(1, 4):
+        _submit(server, small, tag=t)
+    _submit(server, big, tag=100)
+    for t in range(4, 40):
+        _submit(server, small, tag=t)
+    done = _collect(server)
+    assert all(c.status == sgn.SGN_OK for c, _ in done.values())
+    seq = {t: c.admit_seq for t, (c, _) in done.items()}
+    assert sorted(seq.values()) == list(range(1, 41))
+    passed = [t for t in range(4, 40) if seq[t] < seq[100]]
+    print("admission order of the big request", seq[100], "passed by", len(passed))
+    assert len(passed) <= 8
+    server.close()
