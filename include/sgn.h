@@ -97,15 +97,16 @@ typedef struct {
                                  lm_lambda: a step is kept when the mean Huber cost over valid samples
                                  decreases (lambda / 10), otherwise dropped (lambda x 10); a singular system
                                  or an unusable step counts as dropped; lambda stays in [1e-7, 1e7]; one
-                                 extra cost evaluation per solve.  Such plans are solved per plan (not in
-                                 a batch or a server), without texel staging, with square surfels */
+                                 extra cost evaluation per solve.  Such plans run without texel staging,
+                                 with square surfels (in a batch or a server: their own persistent
+                                 launch, with the lane mapping of schedule variant 0) */
     float surfel_radius;      /* 0 (default): surfel s is its P x P tile.  In [0.5, 16]: surfel s is the set
                                  of pixels whose centre lies strictly within this radius of its tile centre
                                  (the paper's circular surfel, Eq. 4; at most 512 pixels); discs of
                                  neighbouring tiles may overlap, and the depth map is then the
                                  depth-buffered render of the discs (Sec. 2.2, as sgn_render_surfels).
-                                 Such plans use 32 lanes per surfel and cannot join a batch, a server or
-                                 sgn_solve_static */
+                                 Such plans use 32 lanes per surfel (in a batch or a server: their own
+                                 persistent launch) and cannot be solved by sgn_solve_static */
 } sgn_plan_desc;
 
 typedef struct sgn_plan sgn_plan;     /* opaque, host side */
@@ -235,17 +236,20 @@ sgn_status sgn_solve_static(const sgn_plan_desc* desc, const double intrinsics[4
 
 /* ---- batches: many keyframe plans in one persistent launch --------------------------- */
 
-/* A batch groups up to max_plans bound plans (any sizes, patches, frame counts, dtypes).
- * sgn_batch_run runs, for every plan, the same work as sgn_solve, in one persistent kernel
- * over a device work list of (plan, surfel range) items, on `cuda_stream`.  The batch needs a
- * small device workspace of its own (sgn_batch_workspace_bytes, after adding the plans). */
+/* A batch groups up to max_plans bound plans (any sizes, patches, frame counts, dtypes, options).
+ * sgn_batch_run runs, for every plan, the same work as sgn_solve, in one persistent kernel per
+ * solver kind present (square surfels with fixed damping; the Marquardt schedule; circular
+ * surfels, whose depth maps are then rendered per plan) over a device work list of (plan, surfel
+ * range) items, on `cuda_stream`.  The batch needs a small device workspace of its own
+ * (sgn_batch_workspace_bytes, after adding the plans). */
 sgn_status sgn_batch_create(int max_plans, sgn_batch** out);
 sgn_status sgn_batch_add(sgn_batch* batch, sgn_plan* plan);
 sgn_status sgn_batch_clear(sgn_batch* batch);
 sgn_status sgn_batch_workspace_bytes(const sgn_batch* batch, size_t* bytes);
 sgn_status sgn_batch_bind(sgn_batch* batch, void* d_workspace, size_t bytes, void* cuda_stream);
-/* Schedule of the persistent launch: variant 0 maps P=4/8/16 surfels to 8/16/32 lanes,
- * variant 1 to 16/32/32 lanes; chunk = surfels per work item (1..65536).  Defaults 0 and 64. */
+/* Schedule of the persistent launches: variant 0 maps P=4/8/16 surfels to 8/16/32 lanes,
+ * variant 1 to 16/32/32 lanes (fixed damping; the other kinds keep their own mapping); chunk =
+ * surfels per work item (1..65536).  Defaults 0 and 64. */
 sgn_status sgn_batch_set_schedule(sgn_batch* batch, int variant, int chunk);
 sgn_status sgn_batch_run(sgn_batch* batch, int iters);
 sgn_status sgn_batch_sync(sgn_batch* batch, uint64_t timeout_ns);

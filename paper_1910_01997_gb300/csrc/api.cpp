@@ -169,12 +169,13 @@ struct sgn_batch {
     int chunk = 64;
     bool dirty = true;
     int n_items = 0;
+    int kind_begin[sgn::kBatchKinds + 1] = {0, 0, 0, 0};  // work-list range of each solver kind
     std::vector<PlanParams> h_plans;
     std::vector<WorkItem> h_items;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_iters = -1;
-    int graph_grid = 0;
+    int graph_grid = 0;  // blocks of the fixed-damping launch
     int graph_frames = 0;  // largest frame count the captured launch sizes its scratch for
     cudaEvent_t done = nullptr;
     std::vector<cudaEvent_t> plan_events;
@@ -848,8 +849,6 @@ static void batch_drop_graph(sgn_batch* b) {
 sgn_status sgn_batch_add(sgn_batch* b, sgn_plan* p) {
     if (!b || !p) return fail(SGN_ERR_INVALID_ARGUMENT, "batch/plan is NULL");
     if (int(b->plans.size()) >= b->max_plans) return fail(SGN_ERR_INVALID_ARGUMENT, "batch is full (%d plans)", b->max_plans);
-    if (!p->disc.empty()) return fail(SGN_ERR_INVALID_ARGUMENT, "circular surfels are solved per plan, not in a batch");
-    if (p->desc.lm_adaptive) return fail(SGN_ERR_INVALID_ARGUMENT, "the Marquardt schedule is solved per plan, not in a batch");
     b->plans.push_back(p);
     b->dirty = true;
     return SGN_OK;
@@ -954,18 +953,24 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
             for (int f = 0; f < p->S; f += b->chunk)
                 b->h_items.push_back(WorkItem{int(i), f, std::min(b->chunk, p->S - f), 0});
         }
-        // Items of one patch size run the same code path: grouping them (largest patch first) keeps
-        // the warps of an SM on one solver variant at a time; within a group, largest cost first.
+        // Items of one solver kind form one contiguous range (one launch per kind).  Items of one
+        // patch size run the same code path: grouping them (largest patch first) keeps the warps of an
+        // SM on one solver variant at a time; within a group, largest cost first.
+        auto kind_of = [&](const WorkItem& w) { return sgn::batch_kind(b->h_plans[w.plan]); };
         std::stable_sort(b->h_items.begin(), b->h_items.end(), [&](const WorkItem& a, const WorkItem& c) {
             const sgn_plan* pa = b->plans[a.plan];
             const sgn_plan* pc = b->plans[c.plan];
+            if (kind_of(a) != kind_of(c)) return kind_of(a) < kind_of(c);
             if (pa->desc.patch != pc->desc.patch) return pa->desc.patch > pc->desc.patch;
             const double ca = double(a.count) * pa->desc.patch * pa->desc.patch * std::max(1, pa->F);
             const double cc = double(c.count) * pc->desc.patch * pc->desc.patch * std::max(1, pc->F);
             return ca > cc;
         });
         b->n_items = int(b->h_items.size());
-        batch_drop_graph(b);  // the captured launch holds the item count
+        for (int k = 0; k <= sgn::kBatchKinds; ++k) b->kind_begin[k] = 0;
+        for (const WorkItem& w : b->h_items) b->kind_begin[kind_of(w) + 1]++;
+        for (int k = 0; k < sgn::kBatchKinds; ++k) b->kind_begin[k + 1] += b->kind_begin[k];
+        batch_drop_graph(b);  // the captured launches hold the item counts
         e = cudaMemcpyAsync(b->ws + off_items, b->h_items.data(), b->h_items.size() * sizeof(WorkItem),
                             cudaMemcpyHostToDevice, b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "work list upload");
@@ -981,9 +986,14 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
         batch_drop_graph(b);
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-        const int per_sm = sgn::batch_blocks_per_sm(b->variant, 256, fmax);
-        if (per_sm <= 0) return fail(SGN_ERR_CUDA, "batch kernel cannot be resident");
-        b->graph_grid = sms * per_sm;
+        int grids[sgn::kBatchKinds] = {0, 0, 0};
+        for (int k = 0; k < sgn::kBatchKinds; ++k) {
+            if (b->kind_begin[k + 1] == b->kind_begin[k]) continue;
+            const int per_sm = sgn::batch_blocks_per_sm(k, b->variant, 256, fmax);
+            if (per_sm <= 0) return fail(SGN_ERR_CUDA, "batch kernel cannot be resident");
+            grids[k] = sms * per_sm;
+        }
+        b->graph_grid = grids[sgn::kBatchFixed];
         cudaStream_t cap = b->stream;
         bool own = false;
         if (cap == nullptr || cap == cudaStreamLegacy) {
@@ -995,9 +1005,17 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
             if (own) cudaStreamDestroy(cap);
             return cuda_fail(e, "cudaStreamBeginCapture");
         }
-        int le = sgn::launch_gn_batch(reinterpret_cast<const PlanParams*>(b->ws), reinterpret_cast<const WorkItem*>(b->ws + off_items),
-                                      b->n_items, reinterpret_cast<int*>(b->ws + off_counter), iters, b->variant,
-                                      b->graph_grid, 256, fmax, cap);
+        // one persistent launch per solver kind present, each over its range of the work list with its
+        // own counter (the launches run one after another on the stream)
+        int le = 0;
+        for (int k = 0; k < sgn::kBatchKinds && !le; ++k) {
+            const int n = b->kind_begin[k + 1] - b->kind_begin[k];
+            if (n == 0) continue;
+            le = sgn::launch_gn_batch(k, reinterpret_cast<const PlanParams*>(b->ws),
+                                      reinterpret_cast<const WorkItem*>(b->ws + off_items) + b->kind_begin[k], n,
+                                      reinterpret_cast<int*>(b->ws + off_counter) + k, iters, b->variant, grids[k], 256,
+                                      fmax, cap);
+        }
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cap, &graph);
         if (own) cudaStreamDestroy(cap);
@@ -1015,7 +1033,17 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
         b->graph_frames = fmax;
     }
     if ((e = cudaGraphLaunch(b->exec, b->stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-    sgn::count_launch();
+    int kinds = 0;
+    for (int k = 0; k < sgn::kBatchKinds; ++k) kinds += b->kind_begin[k + 1] > b->kind_begin[k];
+    sgn::count_launch(uint64_t(kinds));
+    // circular surfels may overlap: each such plan's depth map is the depth-buffered render of its
+    // solved discs (Sec. 2.2), launched here with the plan's current parameters
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        if (b->plans[i]->disc.empty()) continue;
+        const int le = sgn::launch_render_discs(b->h_plans[i], b->stream);
+        if (le) return cuda_fail(le, "disc render launch");
+        sgn::count_launch(2);
+    }
     // Later work on each plan's stream (reads) waits for the batch.
     if ((e = cudaEventRecord(b->done, b->stream)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     for (cudaStream_t s : streams)

@@ -9,12 +9,13 @@
 
 namespace sgn {
 
-// Copy the plan parameters into shared memory (all threads of the block).
+// Copy the plan parameters into shared memory (all threads of the block): the fields before the
+// frame poses and the poses of the frames in use (the unused slots are never read).
 __device__ __forceinline__ void load_plan(PlanParams* dst, const PlanParams* src) {
-    static_assert(sizeof(PlanParams) % 4 == 0, "plan params are copied as words");
     const int* s = reinterpret_cast<const int*>(src);
     int* d = reinterpret_cast<int*>(dst);
-    for (int i = threadIdx.x; i < int(sizeof(PlanParams) / 4); i += blockDim.x) d[i] = s[i];
+    const int n = plan_words(src->F);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
 }
 
 // Minimum resident 256-thread blocks per SM (register budget 85 / 128 / 255 per thread) by pixels

@@ -241,6 +241,7 @@ sgn_status launch_epoch(sgn_server* s, std::vector<Job*>& jobs, Epoch* ep) {
     std::stable_sort(s->h_items.begin(), s->h_items.end(), [&](const sgn::WorkItem& a, const sgn::WorkItem& b) {
         const sgn::PlanParams& pa = s->h_plans[a.plan];
         const sgn::PlanParams& pb = s->h_plans[b.plan];
+        if (sgn::batch_kind(pa) != sgn::batch_kind(pb)) return sgn::batch_kind(pa) < sgn::batch_kind(pb);  // one launch per kind
         if (pa.P != pb.P) return pa.P > pb.P;  // one solver variant at a time (see the batch work list)
         return double(a.count) * pa.P * pa.P * pa.F > double(b.count) * pb.P * pb.P * pb.F;
     });
@@ -256,12 +257,20 @@ sgn_status launch_epoch(sgn_server* s, std::vector<Job*>& jobs, Epoch* ep) {
         return srv_error(SGN_ERR_CUDA, "server: table upload");
     int fmax = 1;
     for (const sgn::PlanParams& pp : s->h_plans) fmax = std::max(fmax, pp.F);
-    const int grid = s->sms * std::max(1, sgn::batch_blocks_per_sm(0, 256, fmax));
-    int le = sgn::launch_gn_batch(reinterpret_cast<const sgn::PlanParams*>(base),
-                                  reinterpret_cast<const sgn::WorkItem*>(items), int(s->h_items.size()), counter,
-                                  jobs[0]->req.iters, 0, grid, 256, fmax, s->compute);
-    if (le) return srv_error(SGN_ERR_CUDA, std::string("server: batch launch: ") + cudaGetErrorString(cudaError_t(le)));
-    sgn::count_launch();
+    // one persistent launch per solver kind present (items sorted by kind), each with its own counter
+    int begin = 0;
+    for (int k = 0; k < sgn::kBatchKinds; ++k) {
+        int end = begin;
+        while (end < int(s->h_items.size()) && sgn::batch_kind(s->h_plans[s->h_items[end].plan]) == k) ++end;
+        if (end == begin) continue;
+        const int grid = s->sms * std::max(1, sgn::batch_blocks_per_sm(k, 0, 256, fmax));
+        const int le = sgn::launch_gn_batch(k, reinterpret_cast<const sgn::PlanParams*>(base),
+                                            reinterpret_cast<const sgn::WorkItem*>(items) + begin, end - begin, counter + k,
+                                            jobs[0]->req.iters, 0, grid, 256, fmax, s->compute);
+        if (le) return srv_error(SGN_ERR_CUDA, std::string("server: batch launch: ") + cudaGetErrorString(cudaError_t(le)));
+        sgn::count_launch();
+        begin = end;
+    }
     if (cudaEventCreateWithFlags(&ep->done, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(ep->done, s->compute) != cudaSuccess)
         return srv_error(SGN_ERR_CUDA, "server: epoch event");
     ep->jobs = jobs;
@@ -430,7 +439,7 @@ sgn_status sgn_server_create(void* d_arena, size_t arena_bytes, int max_slots, i
     s->max_slots = max_slots;
     s->max_items = max_surfels_per_epoch / s->chunk + max_slots;
     s->table_bytes = (size_t(max_slots) * sizeof(sgn::PlanParams) + size_t(s->max_items) * sizeof(sgn::WorkItem) +
-                      sizeof(int) + sgn::kAlign - 1) / sgn::kAlign * sgn::kAlign;
+                      sgn::kBatchKinds * sizeof(int) + sgn::kAlign - 1) / sgn::kAlign * sgn::kAlign;
     if (arena_bytes < 4 * s->table_bytes) {
         delete s;
         return srv_error(SGN_ERR_WORKSPACE_TOO_SMALL, "server: arena too small for its launch tables");
@@ -456,8 +465,6 @@ sgn_status sgn_server_create(void* d_arena, size_t arena_bytes, int max_slots, i
 sgn_status sgn_server_submit(sgn_server* s, const sgn_request* r) {
     if (!s || !r) return srv_error(SGN_ERR_INVALID_ARGUMENT, "server: NULL argument");
     const sgn_plan_desc& d = r->desc;
-    if (d.surfel_radius != 0.0f || d.lm_adaptive)
-        return srv_error(SGN_ERR_INVALID_ARGUMENT, "server: requests use square surfels and the fixed damping");
     sgn_plan* probe = nullptr;
     sgn_status st = sgn_plan_create(&d, &probe);  // validates the description
     if (st != SGN_OK) return st;

@@ -101,6 +101,13 @@ struct PlanParams {
     FramePose frames[kMaxFrames];
 };
 
+// 32-bit words of a PlanParams up to and including the poses of its first F frames (the part a kernel
+// copies into shared memory).
+static_assert(sizeof(PlanParams) % 4 == 0 && sizeof(FramePose) % 4 == 0, "plan params are copied as words");
+SGN_HD constexpr int plan_words(int F) {
+    return int((offsetof(PlanParams, frames) + size_t(F < 0 ? 0 : (F > kMaxFrames ? kMaxFrames : F)) * sizeof(FramePose)) / 4);
+}
+
 // ---- shared-memory staging of frame texels
 // Each (surfel, frame) stages a box of texels around the tile centre's reference projection
 // U_ref = (X_int + X_frac, Y_int + Y_frac): rows Y_int - R .. Y_int + R + 1 and columns from
@@ -169,11 +176,21 @@ struct WorkItem {
     int count;    // number of surfels
     int pad;
 };
-// variant 0: lanes per surfel P4->8, P8->16, P16->32; variant 1: P4->16, P8->32, P16->32.
+// Solver kinds of batched execution: one persistent kernel per kind present in a batch, each over a
+// contiguous range of the work list.
+enum BatchKind : int {
+    kBatchFixed = 0,     // square surfels, fixed damping
+    kBatchAdaptive = 1,  // square surfels, Marquardt schedule (lm_adaptive)
+    kBatchDisc = 2,      // circular surfels (surfel_radius > 0)
+    kBatchKinds = 3
+};
+inline int batch_kind(const PlanParams& pp) { return pp.disc_n > 0 ? kBatchDisc : (pp.lm_adaptive ? kBatchAdaptive : kBatchFixed); }
+// variant (fixed damping only; the other kinds use variant 0): lanes per surfel P4->8, P8->16,
+// P16->32 (0) or P4->16, P8->32, P16->32 (1); circular surfels take one warp per surfel.
 // max_frames: the largest frame count of the batch's plans (sizes the shared-memory scratch).
-int launch_gn_batch(const PlanParams* d_plans, const WorkItem* d_items, int n_items, int* d_counter, int iters,
+int launch_gn_batch(int kind, const PlanParams* d_plans, const WorkItem* d_items, int n_items, int* d_counter, int iters,
                     int variant, int grid, int block_threads, int max_frames, void* stream);
-int batch_blocks_per_sm(int variant, int block_threads, int max_frames);
+int batch_blocks_per_sm(int kind, int variant, int block_threads, int max_frames);
 int lanes_for_patch(int variant, int P);
 
 void count_launch(uint64_t n = 1);

@@ -101,8 +101,15 @@ def oracle_solve_planes(prob, planes, iters, **opts):
     return out
 
 
+# A surfel is stable when every re-run of the oracle stays within this fraction of the tolerance: the
+# GPU is one more sample of the same rounding-scale perturbations, and over the compared surfels of
+# the full-size workloads its deviation stays within three times the largest re-run deviation for
+# all but a few in ten thousand surfels.
+STABLE_FRACTION = 1.0 / 3.0
+
+
 def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=FP32_INPUT_EPS, seeds=(1, 2, 3),
-                  planes=None, step_seeds=(11, 12), **opts):
+                  planes=None, step_seeds=(11, 12), frac_tol=STABLE_FRACTION, **opts):
     """Surfels whose oracle result after `iters` iterations is a stable function of the inputs.
 
     The oracle alone is re-run with the initial parameters perturbed by a relative eps (default: one
@@ -113,16 +120,16 @@ def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=FP32_I
     iteration at a time with its parameters rounded to FP32 and perturbed by FP32_STEP_EPS (relative)
     after every iteration.  With `planes` (intensity and gradient planes given to the
     oracle) those planes are perturbed by +-2 FP32 ulp.  A surfel is stable when every re-run keeps
-    its status and stays within half the tolerance of the unperturbed result, and when the path its
+    its status and stays within frac_tol (a third) of the tolerance of the unperturbed result, and when the path its
     parameters travel over the iterations, times the condition number of its scaled normal
-    equations and 1e-6 (the relative FP32 error of one step), stays below half the tolerance:
+    equations and 1e-6 (the relative FP32 error of one step), stays below that fraction of the tolerance:
     element-by-element parity is only defined there.
     """
     prm = oracle_params(**opts)
     stable = np.ones(prob.S, bool)
     kappa = scaled_cond(base["H_last"]) if prm.optimize_normal else np.ones(prob.S)
     with np.errstate(invalid="ignore"):
-        stable &= (base["path_n"] * kappa * 1e-6 <= 0.5 * tol_deg) & (base["path_id"] * kappa * 1e-6 <= 0.5 * tol_depth)
+        stable &= (base["path_n"] * kappa * 1e-6 <= frac_tol * tol_deg) & (base["path_id"] * kappa * 1e-6 <= frac_tol * tol_depth)
     problems = []
     for k in seeds:
         rng = np.random.default_rng([k, 77])
@@ -145,8 +152,8 @@ def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=FP32_I
         n1 /= np.maximum(np.linalg.norm(n1, axis=1, keepdims=True), 1e-30)
         p = ob.solve(prm, iters, id1, n1, prob.state, depth_map=False)
         stable &= (p["status"] == base["status"])
-        stable &= np.abs(p["id"] / np.where(base["id"] != 0, base["id"], 1.0) - 1.0) <= 0.5 * tol_depth
-        stable &= angle_deg(p["n"], base["n"]) <= 0.5 * tol_deg
+        stable &= np.abs(p["id"] / np.where(base["id"] != 0, base["id"], 1.0) - 1.0) <= frac_tol * tol_depth
+        stable &= angle_deg(p["n"], base["n"]) <= frac_tol * tol_deg
     if step_seeds and not prm.lm_adaptive:
         # the parameters perturbed after every iteration (the rounding of the GPU's FP32 state)
         if planes is not None:
@@ -158,10 +165,10 @@ def oracle_stable(prob, iters, tol_depth, tol_deg, base, dtype="f32", eps=FP32_I
                                        FP32_STEP_EPS)
             # each iteration's FP32 sums (relative error ~1e-6) move its step by up to that much
             # times the scaled condition number of the iteration's normal equations
-            stable &= (p["step_err_n"] * 1e-6 <= 0.5 * tol_deg) & (p["step_err_id"] * 1e-6 <= 0.5 * tol_depth)
+            stable &= (p["step_err_n"] * 1e-6 <= frac_tol * tol_deg) & (p["step_err_id"] * 1e-6 <= frac_tol * tol_depth)
             stable &= (p["status"] == base["status"])
-            stable &= np.abs(p["id"] / np.where(base["id"] != 0, base["id"], 1.0) - 1.0) <= 0.5 * tol_depth
-            stable &= angle_deg(p["n"], base["n"]) <= 0.5 * tol_deg
+            stable &= np.abs(p["id"] / np.where(base["id"] != 0, base["id"], 1.0) - 1.0) <= frac_tol * tol_depth
+            stable &= angle_deg(p["n"], base["n"]) <= frac_tol * tol_deg
     return stable
 
 

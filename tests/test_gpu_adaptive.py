@@ -38,15 +38,14 @@ def test_adaptive_never_raises_the_mean_cost():
     assert np.median(ang) < 1.0 and np.median(np.abs(g["id"][ok] / ring.gt_id[ok] - 1)) < 1e-3
 
 
-def test_adaptive_plans_are_solved_per_plan():
-    """The schedule runs in its own kernel instantiation: batches refuse such plans, and so does the
-    combination with circular surfels."""
+def test_adaptive_plans_join_batches_but_not_circular_surfels():
+    """The schedule runs in its own kernel instantiation: a batch takes such plans (their own persistent
+    launch, see test_gpu_batch), while the combination with circular surfels is refused."""
     import paper_1910_01997_gb300 as sgn
 
     p = synth.room_problem(13, W=320, H=240, F=3)
     pl = sgn.Plan(p.W, p.H, p.P, p.F, "f32", lm_adaptive=True)
     b = sgn.Batch(1)
-    with pytest.raises(sgn.SgnError):
-        b.add(pl)
+    b.add(pl)
     with pytest.raises(sgn.SgnError):
         sgn.Plan(p.W, p.H, p.P, p.F, "f32", lm_adaptive=True, surfel_radius=5.0)

@@ -19,10 +19,10 @@ def _problems():
     ]
 
 
-def _plan(prob, dtype):
+def _plan(prob, dtype, **opts):
     import paper_1910_01997_gb300 as sgn
 
-    plan = sgn.Plan(prob.W, prob.H, prob.P, prob.F, dtype)
+    plan = sgn.Plan(prob.W, prob.H, prob.P, prob.F, dtype, **opts)
     plan.set_intrinsics(*prob.cam)
     plan.set_keyframe(prob.keyframe)
     plan.set_frames(prob.frames, prob.poses)
@@ -60,6 +60,51 @@ def test_batch_matches_plain(variant, chunk):
             planes = stored_planes(prob.frames, dt)
             _check(prob, got, oracle_solve_planes(prob, planes, 10), "f32", f"batch {dt} {prob.W}x{prob.H} P{prob.P}",
                    10, frac="noisy_small" if prob.P == 4 else "room", planes=planes)
+
+
+def test_batch_with_adaptive_and_circular_plans():
+    """Plans with the Marquardt schedule (Sec. 2.4) and with circular surfels (Sec. 2.1, Eq. 4) join a
+    batch beside fixed-damping square surfels: one persistent launch per solver kind, and each plan's
+    surfels equal the oracle within the parity tolerances (and its depth map is the render of its
+    discs)."""
+    import paper_1910_01997_gb300 as sgn
+    from test_gpu_parity import _check
+
+    cases = [
+        ("f32", dict(), synth.room_problem(60, W=320, H=240, F=4, P=8)),
+        ("f32", dict(lm_adaptive=True), synth.room_problem(61, W=320, H=240, F=4, P=8)),
+        ("f16g", dict(lm_adaptive=True), synth.room_problem(62, W=640, H=480, F=3, P=8)),
+        ("f32", dict(surfel_radius=5.0), synth.room_problem(63, W=320, H=240, F=4, P=8)),
+        ("f16g", dict(surfel_radius=10.0), synth.room_problem(64, W=320, H=240, F=3, P=16)),
+    ]
+    plans = [_plan(p, dt, **o) for dt, o, p in cases]
+    batch = sgn.Batch(len(plans))
+    for pl in plans:
+        batch.add(pl)
+    launches = sgn.sgn_launch_count()
+    batch.run(10)
+    batch.sync()
+    # fixed, adaptive and circular launches, plus a render (memset-free: 2 kernels) per circular plan
+    assert sgn.sgn_launch_count() == launches + 3 + 2 * 2
+    for (dt, o, prob), pl in zip(cases, plans):
+        got = pl.read_surfels()
+        got["inv_depth"], got["sidx"] = pl.read_depth_map()
+        plain = gpu_solve(prob, 10, dtype=dt, **o)
+        assert np.mean(got["status"] != plain["status"]) < 0.02
+        if "surfel_radius" in o:
+            assert np.array_equal(got["sidx"] >= 0, plain["sidx"] >= 0) or np.mean((got["sidx"] >= 0) != (plain["sidx"] >= 0)) < 0.01
+        oo = dict(radius=o["surfel_radius"]) if "surfel_radius" in o else dict(o)
+        if dt == "f32":
+            ref = oracle_solve(prob, 10, **oo)
+            planes = None
+        else:
+            planes = stored_planes(prob.frames, dt)
+            ref = oracle_solve_planes(prob, planes, 10, **oo)
+        also = ref["decision_margin"] > 1e-4 if o.get("lm_adaptive") else None
+        # 320x240 keyframes at sigma 0.01: the small noisy workloads' fraction
+        frac = "noisy_small"
+        _check(prob, got, ref, "f32", f"batch {dt} {o} {prob.W}x{prob.H} P{prob.P}", 10, frac=frac, planes=planes,
+               also_stable=also, **oo)
 
 
 def test_batch_graph_replay_is_deterministic():

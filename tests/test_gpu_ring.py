@@ -55,7 +55,7 @@ def test_ring_parity_f32(P, noise):
 def test_ring_reduced_precision_gradients(P, noise, dtype):
     """Gradients stored in FP16/BF16 next to the FP32 intensity (8-byte texels, FP32 residuals and
     accumulation): within 1e-3 and 0.1 deg of the FP64 oracle run on the original frames, at the
-    maximum over the oracle-stable surfels (at least 80 % of the usable ones) and, within twice
+    maximum over the oracle-stable surfels (at least 65 % of the usable ones) and, within twice
     that, at the 99th percentile over all usable surfels."""
     prob = ring_problem_640(P, noise)
     g, o = gpu_solve(prob, 10, dtype=dtype), oracle_solve(prob, 10)

@@ -143,3 +143,26 @@ def test_large_request_is_not_starved_by_small_ones():
     print("admission order of the big request", seq[100], "passed by", len(passed))
     assert len(passed) <= 8
     server.close()
+
+
+def test_served_adaptive_and_circular_requests():
+    """Requests with the Marquardt schedule or circular surfels are served in their own persistent
+    launch of an epoch and give the plain per-plan solve's results (same per-surfel arithmetic)."""
+    import paper_1910_01997_gb300 as sgn
+
+    reqs = [(dict(lm_adaptive=1), synth.room_problem(70, W=320, H=240, F=3)),
+            (dict(surfel_radius=5.0), synth.room_problem(71, W=320, H=240, F=3)),
+            (dict(), synth.room_problem(72, W=320, H=240, F=3))]
+    server = sgn.Server(2 << 30)
+    for i, (o, p) in enumerate(reqs):
+        server.submit(p.W, p.H, p.P, p.cam, p.keyframe, list(p.frames), p.poses, p.id0, p.n0, p.state, 10, tag=i + 1, **o)
+    done = _collect(server)
+    for i, (o, p) in enumerate(reqs):
+        c, got = done[i + 1]
+        assert c.status == sgn.SGN_OK
+        ref = gpu_solve(p, 10, **{("lm_adaptive" if k == "lm_adaptive" else k): (bool(v) if k == "lm_adaptive" else v)
+                                   for k, v in o.items()})
+        assert np.mean(got["status"] != ref["status"]) < 0.01
+        m = ((got["status"] & 0x3F) == 0) & ((ref["status"] & 0x3F) == 0)
+        assert np.median(np.abs(got["id"][m] / ref["id"][m] - 1)) < 1e-6, o
+    server.close()
