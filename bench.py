@@ -666,6 +666,12 @@ class StepInstance:
         self.host["frame_list"] = [self.host["frames"][i] for i in range(F)]
         self.host_out = self._outputs(S, H, W, lambda t: t.pin_memory())
         self.sgn = sgn
+        # the end-to-end step's arguments of the C ABI calls, prepared once (page-locked host buffers)
+        import ctypes
+
+        self.e2e_frames = (ctypes.c_void_p * F)(*[f.data_ptr() for f in self.host["frame_list"]])
+        self.e2e_poses = np.ascontiguousarray(np.asarray(prob.poses, dtype=np.float64).reshape(F, 12))
+        self.e2e_out = [self.host_out[k].data_ptr() for k in ("id", "n", "cost", "nres", "status", "depth", "sidx")]
 
     @staticmethod
     def _outputs(S, H, W, place):
@@ -696,11 +702,19 @@ class StepInstance:
         self.post()
 
     def e2e_step(self, sync=True):
-        """The step through the public API from page-locked host buffers, results read back to the
-        host (asynchronously when sync is False: the caller synchronises later)."""
-        self.pre(host=True)
-        self.solve()
-        self.post(host=True)
+        """The step through the public C API from page-locked host buffers (keyframe, frames with their
+        poses, initial surfels in; surfels and depth map out), results read back to the host
+        (asynchronously when sync is False: the caller synchronises later)."""
+        import ctypes
+
+        sgn, h, W = self.sgn, self.plan.handle, self.prob.W
+        sgn.sgn_set_keyframe(h, self.host["kf"].data_ptr(), W * 4, sgn.SGN_HOST)
+        sgn.sgn_set_frames(h, self.prob.F, ctypes.cast(self.e2e_frames, ctypes.c_void_p), W * 4, sgn.SGN_HOST,
+                           self.e2e_poses.ctypes.data)
+        sgn.sgn_init_surfels(h, self.host["id0"].data_ptr(), self.host["n0"].data_ptr(), self.host["state"].data_ptr(),
+                             sgn.SGN_HOST)
+        sgn.sgn_solve(h, WORKLOAD["iterations"])
+        sgn.sgn_read_results(h, *self.e2e_out, sgn.SGN_HOST)
         if sync:
             self.plan.sync()
 
@@ -844,22 +858,31 @@ def run_ours(args):
         # ends when the last step's results are on the host
         for i in range(max(1, args.warmup)):
             insts[i % R].e2e_step()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ranks.barrier()
-        e0.record(stream)
-        for st in streams[1:]:
-            st.wait_event(e0)
-        for i in range(args.steps):
-            insts[i % R].e2e_step(sync=False)
-        for st in streams[1:]:
-            joined = torch.cuda.Event()
-            joined.record(st)
-            stream.wait_event(joined)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ranks.barrier()
-        e2e_ms = ranks.max_ms(e0.elapsed_time(e1))
+
+        def e2e_region() -> float:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ranks.barrier()
+            e0.record(stream)
+            for st in streams[1:]:
+                st.wait_event(e0)
+            for i in range(args.steps):
+                insts[i % R].e2e_step(sync=False)
+            for st in streams[1:]:
+                joined = torch.cuda.Event()
+                joined.record(st)
+                stream.wait_event(joined)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ranks.barrier()
+            return ranks.max_ms(e0.elapsed_time(e1))
+
+        # the host's calls bound this leg, so it is repeated (at least 5 times, about a second) and
+        # the median reported
+        e2e_all = [e2e_region()]
+        while len(e2e_all) < 5 or (sum(e2e_all) < 1000.0 and len(e2e_all) < 200):
+            e2e_all.append(e2e_region())
+        e2e_ms = statistics.median(e2e_all)
     W, H, S = prob.W, prob.H, prob.S
     h2d = prob.keyframe.nbytes + prob.frames.nbytes + S * (4 + 12 + 1)
     d2h = S * (4 + 12 + 4 + 4 + 1) + W * H * 8
@@ -894,7 +917,9 @@ def run_ours(args):
                               "of the solve graph (the kernel alone), averaged over a second pass of the K steps "
                               "with the step split into three graphs")},
         "e2e": {"value": ranks.throughput(res * args.steps, e2e_ms), "unit": "residuals/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "repeats": len(e2e_all),
+                "value_min": ranks.throughput(res * args.steps, max(e2e_all)),
+                "value_max": ranks.throughput(res * args.steps, min(e2e_all)),
                 "note": f"public API calls per step from page-locked host buffers, steps enqueued back to back on "
                         f"{len(streams)} streams (plans alternate), one synchronisation when the last step's results are on the host"},
         "issue": issue_roofline(kern_avg_s, clk, dev),

@@ -45,8 +45,7 @@ __device__ __forceinline__ void run_chunk(const PlanParams* pp, int first, int c
     for (int base = first; base < end; base += SPW) {
         const int s = base + lane / G;
         // passes of at most 4 pixels per lane keep every patch size within the kernel's 128 registers;
-        // all four pixels of a pass gather before use (two at a time in the plain launch: measured
-        // best for each kernel on the benchmark workloads)
+        // all four pixels of a pass gather before use
         gn_surfel<P, G, DT, false, 4, DPPL, LMA, 4>(pp, s < end ? s : pp->S, lane % G, iters, kModeSolve,
                                                      ref + (lane / G) * group_words);
         __syncwarp();
