@@ -863,7 +863,11 @@ sgn_status sgn_batch_clear(sgn_batch* b) {
 
 static size_t batch_items_upper(const sgn_batch* b) {
     size_t n = 0;
-    for (const sgn_plan* p : b->plans) n += (size_t(p->S) + b->chunk - 1) / b->chunk;
+    for (const sgn_plan* p : b->plans) {
+        n += (size_t(p->S) + b->chunk - 1) / b->chunk;
+        if (b->variant == 2 && p->disc.empty() && !p->desc.lm_adaptive)  // square items of a fixed-damping plan
+            n += size_t(sgn::square_items(p->desc.patch, p->desc.width / p->desc.patch, p->desc.height / p->desc.patch));
+    }
     return n;
 }
 
@@ -883,7 +887,7 @@ sgn_status sgn_batch_workspace_bytes(const sgn_batch* b, size_t* bytes) {
 
 sgn_status sgn_batch_set_schedule(sgn_batch* b, int variant, int chunk) {
     if (!b) return fail(SGN_ERR_INVALID_ARGUMENT, "batch is NULL");
-    if (variant != 0 && variant != 1) return fail(SGN_ERR_INVALID_ARGUMENT, "variant must be 0 or 1");
+    if (variant < 0 || variant > 2) return fail(SGN_ERR_INVALID_ARGUMENT, "variant must be 0, 1 or 2");
     if (chunk < 1 || chunk > 65536) return fail(SGN_ERR_INVALID_ARGUMENT, "chunk outside [1, 65536]");
     if (b->variant != variant || b->chunk != chunk) {
         b->variant = variant;
@@ -950,6 +954,18 @@ sgn_status sgn_batch_run(sgn_batch* b, int iters) {
         b->h_items.clear();
         for (size_t i = 0; i < b->plans.size(); ++i) {
             const sgn_plan* p = b->plans[i];
+            if (b->variant == 2 && sgn::batch_kind(b->h_plans[i]) == sgn::kBatchFixed) {
+                // square items: one block's square of tiles each (count = its surfels, for the order)
+                const PlanParams& pp = b->h_plans[i];
+                const int groups = 256 / sgn::lanes_for_patch(2, pp.P);
+                const int n = sgn::square_items(pp.P, pp.TX, pp.TY);
+                for (int q = 0; q < n; ++q) {
+                    int cnt = 0;
+                    for (int g = 0; g < groups; ++g) cnt += sgn::square_surfel(pp.TX, pp.TY, groups, q, g) >= 0;
+                    b->h_items.push_back(WorkItem{int(i), q, cnt, 0});
+                }
+                continue;
+            }
             for (int f = 0; f < p->S; f += b->chunk)
                 b->h_items.push_back(WorkItem{int(i), f, std::min(b->chunk, p->S - f), 0});
         }

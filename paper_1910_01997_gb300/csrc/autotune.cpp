@@ -148,8 +148,9 @@ extern "C" sgn_status sgn_batch_autotune(sgn_batch* batch, int iters, const char
     const int chunks[] = {8, 16, 32, 64, 128, 256};
     float best = 1e30f;
     int bv = 0, bc = 64;
-    for (int var = 0; var < 2; ++var)
+    for (int var = 0; var < 3; ++var)
         for (int ch : chunks) {
+            if (var == 2 && ch != chunks[0]) continue;  // square items: the chunk only applies to other kinds
             sgn_status st = sgn_batch_set_schedule(batch, var, ch);
             if (st != SGN_OK) return st;
             size_t need = 0;

@@ -9,6 +9,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "gn_impl.cuh"
 
 namespace sgn {
@@ -21,8 +23,10 @@ constexpr int kBatchGroups = 4;
 // passes past a plan's disc are skipped at run time.
 constexpr int kBatchDiscPPL = 16;
 
+// Lanes per surfel of the fixed-damping schedules: variants 0 (warp items) and 2 (square items) map
+// P = 4 / 8 / 16 to 8 / 16 / 32 lanes, variant 1 to 16 / 32 / 32.
 __host__ __device__ constexpr int batch_lanes(int variant, int P) {
-    return P == 16 ? 32 : (P == 8 ? (variant == 0 ? 16 : 32) : (variant == 0 ? 8 : 16));
+    return P == 16 ? 32 : (P == 8 ? (variant == 1 ? 32 : 16) : (variant == 1 ? 16 : 8));
 }
 
 // Dynamic shared memory: per warp, kBatchGroups frame scratches of max_frames frames.
@@ -96,6 +100,58 @@ __device__ __forceinline__ void batch_loop(const PlanParams* __restrict__ plans,
             case SGN_BF16G: dispatch_patch<KIND, V, SGN_BF16G>(my, w, lane, iters, wref, group_words); break;
             default: break;
         }
+    }
+}
+
+// The persistent loop over square items (schedule variant 2, fixed damping): a whole block takes one
+// item, a square of neighbouring tiles of one plan (the block's surfels of a plain launch,
+// square_surfel), so that the footprints its warps gather at the same time overlap in L1 as in a plain
+// launch; the block waits for its slowest warp before the next item.
+__device__ __forceinline__ void batch_square_loop(const PlanParams* __restrict__ plans, const WorkItem* __restrict__ items,
+                                                  int n_items, int* __restrict__ counter, int iters, int max_frames,
+                                                  PlanParams* spp, float* sdyn, int* s_item) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int group_words = group_scratch_words(max_frames);
+    float* wref = sdyn + warp * kBatchGroups * group_words;
+    PlanParams* pp = &spp[0];
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = *s_item;
+        if (it >= n_items) break;
+        const WorkItem w = items[it];
+        if (w.plan != cur) {
+            const int* src = reinterpret_cast<const int*>(plans + w.plan);
+            int* dst = reinterpret_cast<int*>(pp);
+            const int n = plan_words(__ldg(&plans[w.plan].F));
+            for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = __ldg(src + i);
+            __syncthreads();
+            cur = w.plan;
+        }
+        auto run = [&](auto p_tag, auto dt_tag) {
+            constexpr int P = decltype(p_tag)::value, DT = decltype(dt_tag)::value, G = batch_lanes(0, P);
+            const int s = square_surfel(pp->TX, pp->TY, kBatchBlock / G, w.first, threadIdx.x / G);
+            gn_surfel<P, G, DT, false, 4, 0, false, 4>(pp, s < 0 ? pp->S : s, lane % G, iters, kModeSolve,
+                                                        wref + (lane / G) * group_words);
+        };
+        auto by_patch = [&](auto dt_tag) {
+            switch (pp->P) {
+                case 4: run(std::integral_constant<int, 4>{}, dt_tag); break;
+                case 8: run(std::integral_constant<int, 8>{}, dt_tag); break;
+                case 16: run(std::integral_constant<int, 16>{}, dt_tag); break;
+                default: break;
+            }
+        };
+        switch (pp->dtype) {
+            case SGN_F32: by_patch(std::integral_constant<int, SGN_F32>{}); break;
+            case SGN_F16: by_patch(std::integral_constant<int, SGN_F16>{}); break;
+            case SGN_BF16: by_patch(std::integral_constant<int, SGN_BF16>{}); break;
+            case SGN_F16G: by_patch(std::integral_constant<int, SGN_F16G>{}); break;
+            case SGN_BF16G: by_patch(std::integral_constant<int, SGN_BF16G>{}); break;
+            default: break;
+        }
+        __syncthreads();  // every warp is done with this item (and with *s_item) before the next
     }
 }
 

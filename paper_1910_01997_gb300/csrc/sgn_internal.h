@@ -192,6 +192,8 @@ int launch_gn_batch(int kind, const PlanParams* d_plans, const WorkItem* d_items
                     int variant, int grid, int block_threads, int max_frames, void* stream);
 int batch_blocks_per_sm(int kind, int variant, int block_threads, int max_frames);
 int lanes_for_patch(int variant, int P);
+// Square items of a fixed-damping plan under schedule variant 2 (a block's square of tiles each).
+int square_items(int P, int TX, int TY);
 
 void count_launch(uint64_t n = 1);
 // Sets the calling thread's sgn_last_error() message and returns st.

@@ -31,7 +31,8 @@ def _stats(prob, g, o, dtype, frac_key):
     tol = TOL["parity"][dtype]
     stable = oracle_stable(prob, 10, tol["depth_rel"], tol["normal_deg"], o, dtype=dtype)
     st = compare(prob, g, o, margin_px=WELL["margin_px"], stable=stable)
-    print(dtype, {k: v for k, v in st.items() if k not in ("rel", "ang", "mask")})
+    print(f"ring {prob.W}x{prob.H} P{prob.P} sigma {prob.noise_sigma} {dtype} vs FP64 oracle",
+          {k: v for k, v in st.items() if k not in ("rel", "ang", "mask")})
     return tol, st, FRAC[frac_key]
 
 
