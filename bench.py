@@ -296,6 +296,12 @@ def batch_leg(dtype: str, stream, dev, reps: int = 5):
             batch.add(pl)
         variant, chunk = batch.autotune(iters)
         ms_batch = timed(lambda: batch.run(iters))
+        per_schedule = {}
+        for v, c in ((0, 8), (0, 64), (1, 8), (1, 64), (2, 8)):
+            batch.set_schedule(v, c)
+            per_schedule[f"variant{v}_chunk{c}"] = res / (timed(lambda: batch.run(iters)) * 1e-3)
+        batch.set_schedule(variant, chunk)
+        batch.run(iters)
         diffs = []
         for pl, ref in zip(plans, plain_out):
             got = pl.read_surfels()
@@ -346,6 +352,7 @@ def batch_leg(dtype: str, stream, dev, reps: int = 5):
             "batched": res / (ms_batch / 1e3), "speedup_vs_plain_graph": ms_graph / ms_batch,
             "plain_graph_4_streams": res / (ms_graph4 / 1e3), "speedup_vs_plain_graph_4_streams": ms_graph4 / ms_batch,
             "schedule": {"variant": variant, "surfels_per_item": chunk},
+            "batched_by_schedule": per_schedule,
             "depth_rel_diff_vs_plain": {"median": float(np.median(diffs)), "p99": float(np.percentile(diffs, 99)),
                                         "frac_above_1e-4": float(np.mean(diffs > 1e-4))},
             "unit": "residuals/s"}

@@ -248,10 +248,11 @@ sgn_status sgn_batch_clear(sgn_batch* batch);
 sgn_status sgn_batch_workspace_bytes(const sgn_batch* batch, size_t* bytes);
 sgn_status sgn_batch_bind(sgn_batch* batch, void* d_workspace, size_t bytes, void* cuda_stream);
 /* Schedule of the persistent launches: variant 0 maps P=4/8/16 surfels to 8/16/32 lanes and
- * variant 1 to 16/32/32 lanes, each warp taking work items of `chunk` surfels (1..65536); variant 2
- * maps as variant 0 but each block takes a square of neighbouring tiles of one plan at a time (the
- * block of a plain launch).  The schedule applies to fixed-damping plans; the other kinds keep their
- * own mapping with chunk-sized items.  Defaults 0 and 64. */
+ * variant 1 to 16/32/32 lanes, each warp taking work items of `chunk` surfels (1..65536) in tile
+ * order; variant 2 maps as variant 0 but each block takes a square of neighbouring tiles of one
+ * plan at a time (the block of a plain launch; `chunk` then applies to the other kinds only).  The
+ * schedule applies to fixed-damping plans; the other kinds keep their own mapping with chunk-sized
+ * items.  Defaults 0 and 64. */
 sgn_status sgn_batch_set_schedule(sgn_batch* batch, int variant, int chunk);
 sgn_status sgn_batch_run(sgn_batch* batch, int iters);
 sgn_status sgn_batch_sync(sgn_batch* batch, uint64_t timeout_ns);

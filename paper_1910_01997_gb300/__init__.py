@@ -652,8 +652,13 @@ class Batch:
 
     def autotune(self, iters, cache_path=None):
         """Bind a workspace large enough for every schedule, then time the schedules (C++ autotuner)."""
-        sgn_batch_set_schedule(self.handle, 0, 8)
-        self._bind()
+        torch = _torch()
+        n = 0
+        for v in (0, 2):  # the larger work list of the schedules tried (chunk 8)
+            sgn_batch_set_schedule(self.handle, v, 8)
+            n = max(n, sgn_batch_workspace_bytes(self.handle))
+        self.workspace = torch.empty(n, dtype=torch.uint8, device="cuda")
+        sgn_batch_bind(self.handle, self.workspace.data_ptr(), n, self.stream.cuda_stream)
         return sgn_batch_autotune(self.handle, iters, cache_path)
 
     def close(self):

@@ -264,7 +264,7 @@ def compare(prob, g, o, margin_px=1e-3, min_normal_eig=None, stable=None):
     rel = np.abs(g["id"].astype(np.float64) / o["id"] - 1.0)
     ang = angle_deg(g["n"], o["n"])
     st = dict(n=int(cmp.sum()), n_usable=int(usable.sum()), excluded=excl,
-              status_mismatch=int((g["status"] != o["status"]).sum()))
+              status_mismatch=int((gs != os_).sum()))  # outcome codes; the high bits are route flags
     for name, m in (("", cmp), ("all_", usable)):
         if m.any():
             st[name + "depth_max"] = float(rel[m].max())

@@ -110,7 +110,7 @@ def test_batch_host_side_checks(sgn):
         sgn.sgn_batch_run(b, 3)
     assert e.value.status == sgn.SGN_ERR_NOT_BOUND
     with pytest.raises(sgn.SgnError):
-        sgn.sgn_batch_set_schedule(b, 2, 64)
+        sgn.sgn_batch_set_schedule(b, 3, 64)
     sgn.sgn_batch_destroy(b)
     sgn.sgn_plan_destroy(h)
 

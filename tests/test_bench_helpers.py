@@ -28,7 +28,7 @@ def test_kernel_hash_ignores_comments_but_not_code(tmp_path):
     text = src.read_text()
     src.write_text("// a new comment line\n" + text.replace("namespace sgn {", "namespace sgn {  /* inline */", 1) + "\n\n")
     assert bench.kernel_sha(root) == h0
-    src.write_text(text.replace("SGN_CHUNK 2", "SGN_CHUNK 3", 1))
+    src.write_text(text + "\nstatic const int kHashProbe = 1;\n")
     assert bench.kernel_sha(root) != h0
 
 

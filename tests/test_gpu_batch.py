@@ -30,7 +30,7 @@ def _plan(prob, dtype, **opts):
     return plan
 
 
-@pytest.mark.parametrize("variant,chunk", [(0, 64), (1, 64), (0, 7)])
+@pytest.mark.parametrize("variant,chunk", [(0, 64), (1, 64), (0, 7), (2, 64), (2, 7)])
 def test_batch_matches_plain(variant, chunk):
     """Each keyframe solved in the mix equals the oracle (and so the plain launch) within the
     parity tolerances, on the surfels where the comparison is defined (see test_gpu_parity)."""
@@ -141,7 +141,7 @@ def test_autotuners_choose_valid_schedules_and_use_the_cache(tmp_path):
     for pl in plans:
         batch.add(pl)
     variant, chunk = batch.autotune(4, cache)
-    assert variant in (0, 1) and chunk in (8, 16, 32, 64, 128, 256)
+    assert variant in (0, 1, 2) and chunk in (8, 16, 32, 64, 128, 256)
     assert batch.autotune(4, cache) == (variant, chunk)
     assert cache.read_text().count("batch|") == 1
     batch.run(4)
