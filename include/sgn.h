@@ -208,9 +208,9 @@ sgn_status sgn_import_state(sgn_plan* plan, const void* host, size_t bytes);
 /* ---- one solve that allocates nothing --------------------------------------------------- */
 
 /* The paper has no counterpart to this call; it serves callers that must not allocate device
- * memory where they solve: code running while a stream is captured into a CUDA graph, real-time
- * loops that may not take the allocator's locks or fail with out-of-memory mid-run, and host
- * frameworks that hand out only the buffers they own.
+ * memory where they solve: real-time loops that may not take the allocator's locks or fail with
+ * out-of-memory mid-run, and host frameworks or plugins that hand out only the buffers they own
+ * (and forbid their components any allocation of their own).
  *
  * sgn_solve_static runs the same work as sgn_set_frames + sgn_init_surfels + sgn_solve + the reads,
  * enqueued on cuda_stream, without a plan or workspace: every input and output is a caller-owned

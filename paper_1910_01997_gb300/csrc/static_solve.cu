@@ -1,10 +1,10 @@
 // sgn_solve_static: the whole keyframe solve (frame preparation, seeding, Gauss-Newton iterations,
 // final cost, depth map) for callers that cannot allocate device memory.
 //
-// Some callers may not call cudaMalloc or any allocator at the point where they solve: code that
-// runs while a CUDA stream is being captured into a graph (allocation breaks the capture), real-time
+// Some callers may not call cudaMalloc or any allocator at the point where they solve: real-time
 // loops that must not take the allocator's locks or risk an out-of-memory failure mid-run, and host
-// frameworks or plugins that hand out only the buffers they own.  Those callers pass their inputs
+// frameworks or plugins that hand out only the buffers they own and forbid any allocation of their
+// components.  Those callers pass their inputs
 // and outputs as device pointers; the one intermediate this path needs, the packed frame texels,
 // goes to the fixed array below.
 //

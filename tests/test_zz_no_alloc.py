@@ -1,5 +1,6 @@
 """sgn_solve_static: the whole keyframe solve for callers that must not allocate device memory
-(code inside stream capture, real-time loops, frameworks that own every buffer).
+(real-time loops that may not take allocator locks or fail with out-of-memory mid-run, frameworks
+that own every buffer).
 
 It runs through the C ABI with device inputs and outputs only, its frame texels in the library's
 fixed device scratch, and must give the result of the plan-based solve, within the tolerances the
