@@ -766,7 +766,7 @@ def issue_roofline(kernel_s: float, clocks: dict, dev):
 
 
 def l1_pipe_roofline(kernel_s: float, clocks: dict, dev):
-    """The resource that binds the Gauss-Newton kernel: its L1/shared-memory load pipeline (ncu
+    """The busiest unit of the Gauss-Newton kernel: its L1/shared-memory load pipeline (ncu
     l1tex__data_pipe_lsu_wavefronts of one launch on the current source: texel gathers, frame-map
     reads, shuffles) per kernel second, against the pipeline's one wavefront per cycle per SM at the
     SM clock sampled during the timed region."""
