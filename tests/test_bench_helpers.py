@@ -42,3 +42,24 @@ def test_committed_counters_match_the_current_kernel():
 def test_single_rank_throughput_and_ms():
     ranks = bench.Ranks("gloo")
     assert ranks.throughput(15_360_000 * 1000, 80.0) == pytest.approx(1.92e11)
+
+
+def test_issue_and_l1_pipe_rooflines(monkeypatch):
+    """The two counter-based rooflines of the bench line: counts of one launch per kernel second
+    against one warp instruction per cycle per SM sub-partition, and one L1 data-pipeline wavefront
+    per cycle per SM, at the sampled clock (152 SMs at 2070 MHz: 1258.56 and 314.64 G/s)."""
+    import types
+
+    import torch
+
+    monkeypatch.setattr(bench, "profiled_counters",
+                        lambda: {"warp_instructions_per_launch": 45.0e6, "l1_lsu_wavefronts_per_launch": 15.0e6})
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: types.SimpleNamespace(multi_processor_count=152))
+    clk = {"sm_mhz": 2070.0}
+    issue = bench.issue_roofline(75e-6, clk, None)
+    assert issue["peak"] == pytest.approx(1258.56) and issue["achieved"] == pytest.approx(600.0)
+    l1 = bench.l1_pipe_roofline(75e-6, clk, None)
+    assert l1["peak"] == pytest.approx(314.64) and l1["achieved"] == pytest.approx(200.0)
+    assert l1["frac"] == pytest.approx(200.0 / 314.64)
+    monkeypatch.setattr(bench, "profiled_counters", lambda: {})
+    assert bench.issue_roofline(75e-6, clk, None) is None and bench.l1_pipe_roofline(75e-6, clk, None) is None
