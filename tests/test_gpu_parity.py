@@ -211,6 +211,29 @@ def test_device_inputs_equal_host_inputs():
         assert np.array_equal(dev[k].cpu().numpy(), host[k]), k
 
 
+def test_host_frame_layouts_give_identical_results():
+    """Host frames stacked in one array, as separate arrays and in a mix of both give the same
+    results bit for bit; each plan sees its frames only in the layout under test."""
+    import paper_1910_01997_gb300 as sgn
+
+    prob = synth.room_problem(11, F=5)
+    stacked = gpu_solve(prob, 4)
+    a = np.ascontiguousarray(prob.frames[:2])
+    b = np.ascontiguousarray(prob.frames[3:])
+    layouts = ([np.array(f, copy=True) for f in prob.frames], [a[0], a[1], np.array(prob.frames[2], copy=True), b[0], b[1]])
+    for frames in layouts:
+        plan = sgn.Plan(prob.W, prob.H, prob.P, prob.F)
+        plan.set_intrinsics(*prob.cam)
+        plan.set_keyframe(prob.keyframe)
+        plan.set_frames(frames, prob.poses)
+        plan.init_surfels(prob.id0, prob.n0, prob.state)
+        plan.solve(4)
+        out = plan.read_surfels()
+        out["inv_depth"], out["sidx"] = plan.read_depth_map()
+        for k in ("id", "n", "cost", "nres", "status", "inv_depth", "sidx"):
+            assert np.array_equal(out[k], stacked[k], equal_nan=True), k
+
+
 def test_read_results_equals_separate_readbacks():
     """sgn_read_results (one call; one copy kernel for device memory) returns what sgn_read_surfels
     and sgn_read_depth_map return, into device and into host memory, with any pointer left NULL."""
